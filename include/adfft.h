@@ -1,0 +1,190 @@
+/*
+ * adfft: the alpha-densified DFT on NVIDIA GB300 (sm_103a).
+ *
+ * For N samples x_n of a record of length T (t_n = nT/N, Eq. 3) and a dense
+ * sampling factor alpha with M = alpha*N an integer, the library computes the
+ * M output bins (Sec. 2, Eqs. 6-7, with the T/N scale of Eq. 2)
+ *
+ *     X_m = S * sum_{n=0}^{N-1} x_n * exp(-2*pi*i * m*n / M),   m = 0 .. M-1,
+ *
+ * whose bin interval is 1/(alpha*T).  S defaults to T/N with T = 1 (that is,
+ * 1/N); adfft_plan_set_scale(plan, 1.0) gives Eq. 7 exactly as printed.  The
+ * sign convention is W_M^{mn} = exp(-2 pi i m n / M) (Sec. 3).  For alpha > 1
+ * this equals the length-M DFT of x zero-padded to M (Sec. 2); for alpha < 1 it
+ * is the "one-way" transform of Sec. 2.
+ *
+ * Fast form (Sec. 3, Eqs. 9-15, written in the decimation-in-frequency order):
+ * with g = gcd(M, N), P = M/g and q = N/g, bin m = P*k + r (k < g, r < P) is
+ *     X_{Pk+r} = S * FFT_g( sum_{f<q} x_{n+g f} W_M^{r (n + g f)} )[k],
+ * i.e. P twiddled length-g FFTs (q = 1 for integer alpha, which is the
+ * "twiddle by W_M^{rn}, then alpha length-N FFTs" form).  Lengths g that are
+ * not a power of two, or too large a fold q, use a chirp-z (Bluestein)
+ * evaluation of the same sum.  Real input is packed two samples per complex
+ * element and unpacked in the output epilogue.
+ *
+ * Conventions for every entry point:
+ *   - Device buffers and the CUDA stream belong to the caller.  The plan owns
+ *     its twiddle/chirp tables and any workspace; both live in device memory
+ *     allocated by adfft_plan_create* and freed by adfft_plan_destroy.
+ *   - Execution is stream-ordered and asynchronous; a plan may run on one
+ *     stream at a time (calls on different streams that overlap race on the
+ *     plan's workspace).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Data layout: input [batch][N] contiguous (real: float/double; complex:
+ *     interleaved re,im); output [batch][M] complex, bins in natural order
+ *     m = 0..M-1 (bins above M/2 are the negative frequencies).  Real input
+ *     still yields all M bins.  Device pointers must be 16-byte aligned.
+ *   - Every call returns ADFFT_OK (0) or a negative adfft_status; a call that
+ *     fails launches nothing.  No C++ exception crosses this interface.
+ */
+#ifndef ADFFT_H
+#define ADFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADFFT_ABI_VERSION 1
+
+typedef struct adfft_plan_s *adfft_plan_t;
+
+/* Input element type; the output is complex of the same precision. */
+typedef enum {
+    ADFFT_R32 = 0,  /* real float32 input   -> complex64 (float2) output  */
+    ADFFT_C64 = 1,  /* complex64 input      -> complex64 output           */
+    ADFFT_R64 = 2,  /* real float64 input   -> complex128 (double2) output */
+    ADFFT_C128 = 3  /* complex128 input     -> complex128 output          */
+} adfft_dtype_t;
+
+typedef enum {
+    ADFFT_OK = 0,
+    ADFFT_ERR_INVALID_ARG = -1,      /* NULL plan/pointer, N < 1, batch < 0, bad enum */
+    ADFFT_ERR_INVALID_ALPHA = -2,    /* alpha not finite or <= 0, or alpha*N not an integer */
+    ADFFT_ERR_UNSUPPORTED_SIZE = -3, /* sizes beyond what any kernel of the plan handles */
+    ADFFT_ERR_MISALIGNED = -4,       /* a device pointer is not 16-byte aligned */
+    ADFFT_ERR_OVERLAP = -5,          /* input and output ranges overlap (no in-place form) */
+    ADFFT_ERR_CUDA = -6,             /* CUDA runtime or launch error */
+    ADFFT_ERR_OOM = -7,              /* device allocation failed */
+    ADFFT_ERR_TIMEOUT = -8,          /* a bounded device-side wait expired */
+    ADFFT_ERR_NOT_SUPPORTED = -9     /* the plan's configuration lacks this operation */
+} adfft_status_t;
+
+/* Algorithm choice (adfft_plan_set_algorithm). */
+typedef enum {
+    ADFFT_ALGO_AUTO = 0,       /* fold+FFT when g = gcd(M,N) is a power of two and q is small, else chirp-z */
+    ADFFT_ALGO_FOLD = 1,       /* P twiddled length-g FFTs (integer alpha: q = 1) */
+    ADFFT_ALGO_BLUESTEIN = 2   /* chirp-z: mn = (m^2 + n^2 - (m-n)^2)/2, convolution by FFT */
+} adfft_algo_t;
+
+/* Arithmetic form of the length-g FFT stages (adfft_plan_set_precision). */
+typedef enum {
+    ADFFT_PREC_NATIVE = 0,     /* FP32 for R32/C64 plans, FP64 for R64/C128 plans */
+    ADFFT_PREC_FP16X2 = 1,     /* tensor-core radix-16 stages, fp16 hi+lo split operands, FP32 accumulate */
+    ADFFT_PREC_BF16X3 = 2      /* tensor-core radix-16 stages, bf16 hi+lo split operands, FP32 accumulate */
+} adfft_precision_t;
+
+/* Read-only description of a plan (adfft_plan_get_info). */
+typedef struct {
+    int64_t N;            /* samples per signal */
+    int64_t M;            /* output bins per signal, M = alpha*N */
+    int64_t batch;        /* signals (ragged plans: count) */
+    int32_t dtype;        /* adfft_dtype_t */
+    int32_t algo;         /* algorithm actually used (adfft_algo_t, never AUTO) */
+    int64_t fft_len;      /* g: length of each sub-FFT (Bluestein: the padded length L) */
+    int64_t residues;     /* P = M/g sub-FFTs per signal (Bluestein: output chunks) */
+    int64_t fold;         /* q = N/g (Bluestein: 0) */
+    int32_t cluster;      /* CTAs per signal sharing one thread-block cluster */
+    int32_t passes;       /* HBM passes per forward transform (1 = fused single pass) */
+    double scale;         /* S */
+} adfft_plan_info_t;
+
+/*
+ * Create a plan for `batch` signals of N samples and dense sampling factor
+ * alpha (Eq. 6), M = alpha*N bins each.  alpha*N must be an integer to within
+ * 1e-9*alpha*N (it is rounded to the nearest integer); alpha may be below 1.
+ * Returns NULL on failure; adfft_last_error() then gives the reason.
+ * Allocates the plan's tables (and workspace, if its algorithm needs one) on
+ * the current CUDA device.
+ */
+adfft_plan_t adfft_plan_create(int64_t N, double alpha, int64_t batch, int dtype);
+
+/* Same as adfft_plan_create with the bin count M given exactly (alpha = M/N). */
+adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dtype);
+
+/*
+ * Ragged plan: `count` signals with their own N[i] and alpha[i] (each as in
+ * adfft_plan_create), packed back to back: signal i occupies input elements
+ * [in_off[i], in_off[i] + N[i]) and output bins [out_off[i], out_off[i] + M[i]),
+ * offsets as returned by adfft_plan_offsets.  The forward transform of the
+ * whole set is one persistent kernel launch over a queue of (signal, residue
+ * group) tiles, replayed from a CUDA graph captured at the first execute on
+ * a given stream.  Only ADFFT_R32 and ADFFT_C64 are accepted.
+ */
+adfft_plan_t adfft_plan_create_ragged(const int64_t *N, const double *alpha, int64_t count,
+                                      int dtype);
+
+/* Packed offsets of a ragged plan (arrays of count+1 entries; either may be NULL).
+ * For a uniform plan: in_off[i] = i*N, out_off[i] = i*M. */
+int adfft_plan_offsets(adfft_plan_t plan, int64_t *in_off, int64_t *out_off);
+
+/* Status code of the last failed adfft_plan_create* on this thread (ADFFT_OK if none). */
+int adfft_last_error(void);
+
+/* Static, human-readable name of a status code. */
+const char *adfft_status_string(int status);
+
+/* Free the plan's device tables, workspace and graphs.  NULL is accepted.
+ * Synchronises the device first so no launch of the plan is still running. */
+int adfft_plan_destroy(adfft_plan_t plan);
+
+/* Set the scale S (default 1/N, i.e. T/N with T = 1; S = T/N for a record of length T). */
+int adfft_plan_set_scale(adfft_plan_t plan, double S);
+
+/* Choose the algorithm; ADFFT_ERR_NOT_SUPPORTED if it cannot serve this plan's sizes. */
+int adfft_plan_set_algorithm(adfft_plan_t plan, int algo);
+
+/* Choose the FFT-stage arithmetic (adfft_precision_t); ADFFT_ERR_NOT_SUPPORTED if
+ * the plan's dtype or algorithm has no such form. */
+int adfft_plan_set_precision(adfft_plan_t plan, int mode);
+
+/* Fill *info; ADFFT_ERR_INVALID_ARG for NULL arguments. */
+int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t *info);
+
+/* Device workspace bytes the plan holds (0 for the fused single-pass form). */
+size_t adfft_plan_workspace_bytes(adfft_plan_t plan);
+
+/*
+ * Forward transform of the whole batch: d_in [batch][N] (input dtype),
+ * d_out [batch][M] complex.  Both device pointers, 16-byte aligned, not
+ * overlapping.  Asynchronous on `stream`.
+ */
+int adfft_execute(adfft_plan_t plan, const void *d_in, void *d_out, void *stream);
+
+/*
+ * Adjoint (conjugate-transpose) transform, the backward pass of adfft_execute:
+ *     d_grad_in[n] = S * sum_m exp(+2 pi i m n / M) * d_grad_out[m]
+ * for complex plans, and its real part for real plans (the adjoint with
+ * respect to the real inner product, which is what a gradient needs).  With
+ * S = 1/(alpha N) this is the inverse transform in the second line of Eq. 7.
+ * d_grad_out [batch][M] complex; d_grad_in [batch][N] of the input dtype.
+ */
+int adfft_execute_adjoint(adfft_plan_t plan, const void *d_grad_out, void *d_grad_in,
+                          void *stream);
+
+/*
+ * End-to-end forward transform from HOST memory: copies h_in to the device,
+ * runs adfft_execute, copies the spectrum back to h_out and synchronises the
+ * stream.  The device staging buffers are allocated by the plan on first use
+ * and kept until adfft_plan_destroy.  Host buffers should be page-locked for
+ * full copy bandwidth.
+ */
+int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADFFT_H */

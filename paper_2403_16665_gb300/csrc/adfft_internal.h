@@ -1,0 +1,61 @@
+// Internal plan representation and kernel launchers of the adfft library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/adfft.h"
+#include "fft_device.cuh"
+#include "fused.cuh"
+
+namespace adfft {
+
+// Launch geometry of the fused single-pass kernel.
+struct FusedLaunch {
+  FusedArgs args;
+  int mode;        // LoadMode
+  int r0;          // radix of the first pass
+  bool dbl;        // double2 (true) or float2 elements
+  int threads;
+  int grid_y;
+  size_t smem;
+};
+
+struct Plan {
+  int64_t N = 0, M = 0, batch = 0;
+  int dtype = 0;
+  bool real = false, dbl = false;
+  int algo = ADFFT_ALGO_FOLD;
+  int precision = ADFFT_PREC_NATIVE;
+  double scale = 1.0;
+  int device = 0;
+  size_t in_elem = 0, out_elem = 0;   // bytes per input scalar/complex, per output complex
+
+  // fold + FFT (fused) path
+  bool fold_ok = false;
+  FusedLaunch fused{};
+  void* d_tw = nullptr;               // twiddle table of the fused path
+
+  // host-memory staging of adfft_execute_host
+  void* d_stage_in = nullptr;
+  void* d_stage_out = nullptr;
+
+  // packed offsets (uniform plans: i*N, i*M)
+  std::vector<int64_t> in_off, out_off;
+
+  size_t in_bytes() const { return (size_t)batch * (size_t)N * in_elem; }
+  size_t out_bytes() const { return (size_t)batch * (size_t)M * out_elem; }
+};
+
+// Kernel launchers (fused.cu).  Return a cudaError_t.
+cudaError_t fused_prepare(const FusedLaunch& L);   // sets function attributes once
+cudaError_t fused_launch(const FusedLaunch& L, const void* in, void* out, cudaStream_t stream);
+int fused_max_active_clusters(const FusedLaunch& L);
+
+}  // namespace adfft
+
+struct adfft_plan_s {
+  adfft::Plan p;
+};

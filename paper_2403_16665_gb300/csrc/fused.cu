@@ -1,0 +1,96 @@
+// Instantiations and launchers of the fused single-pass forward kernel.
+#include "adfft_internal.h"
+
+namespace adfft {
+
+namespace {
+
+constexpr int kVptF32 = 32;   // complex values per thread per pass, float2
+constexpr int kVptF64 = 16;   // complex values per thread per pass, double2
+
+using KernelFn = void (*)(const FusedArgs);
+
+template <typename V, int MODE, int VPT>
+KernelFn pick_r0(int r0) {
+  switch (r0) {
+    case 1: return fused_forward_kernel<V, MODE, VPT, 1>;
+    case 2: return fused_forward_kernel<V, MODE, VPT, 2>;
+    case 4: return fused_forward_kernel<V, MODE, VPT, 4>;
+    case 8: return fused_forward_kernel<V, MODE, VPT, 8>;
+    default: return fused_forward_kernel<V, MODE, VPT, 16>;
+  }
+}
+
+KernelFn pick_kernel(const FusedLaunch& L) {
+  if (L.dbl) {
+    switch (L.mode) {
+      case kLoadComplex: return pick_r0<double2, kLoadComplex, kVptF64>(L.r0);
+      case kLoadRealPacked: return pick_r0<double2, kLoadRealPacked, kVptF64>(L.r0);
+      default: return pick_r0<double2, kLoadRealPlain, kVptF64>(L.r0);
+    }
+  }
+  switch (L.mode) {
+    case kLoadComplex: return pick_r0<float2, kLoadComplex, kVptF32>(L.r0);
+    case kLoadRealPacked: return pick_r0<float2, kLoadRealPacked, kVptF32>(L.r0);
+    default: return pick_r0<float2, kLoadRealPlain, kVptF32>(L.r0);
+  }
+}
+
+}  // namespace
+
+int fused_values_per_thread(bool dbl) { return dbl ? kVptF64 : kVptF32; }
+
+cudaError_t fused_prepare(const FusedLaunch& L) {
+  KernelFn k = pick_kernel(L);
+  // the attribute is per kernel and shared by every plan: always allow the full 227 KiB
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  if (L.args.C > 8) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int fused_max_active_clusters(const FusedLaunch& L) {
+  KernelFn k = pick_kernel(L);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.args.C, L.grid_y, 1);
+  cfg.blockDim = dim3(L.threads, 1, 1);
+  cfg.dynamicSmemBytes = L.smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = L.args.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return n;
+}
+
+cudaError_t fused_launch(const FusedLaunch& L, const void* in, void* out, cudaStream_t stream) {
+  KernelFn k = pick_kernel(L);
+  FusedArgs a = L.args;
+  a.in = in;
+  a.out = out;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.C, L.grid_y, 1);
+  cfg.blockDim = dim3(L.threads, 1, 1);
+  cfg.dynamicSmemBytes = L.smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = a.C > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, a);
+}
+
+}  // namespace adfft

@@ -1,0 +1,414 @@
+// Host side of the adfft C ABI: plan validation, algorithm and launch-shape
+// selection, FP64-derived tables, and the extern "C" entry points.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "adfft_internal.h"
+
+namespace adfft {
+
+int fused_values_per_thread(bool dbl);
+
+namespace {
+
+thread_local int g_last_error = ADFFT_OK;
+
+constexpr size_t kSmemLimit = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
+constexpr int kMaxCluster = 16;             // non-portable cluster size limit
+constexpr int kMaxFold = 64;                // largest fold factor q the fused kernel takes
+constexpr int kMaxThreads = 512;
+
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+// exp(-2 pi i e / Mt) in double precision, e reduced to the symmetric range first.
+void root_of_unity(int64_t e, int64_t Mt, double* c, double* s) {
+  e %= Mt;
+  if (e < 0) e += Mt;
+  int64_t k = (2 * e > Mt) ? e - Mt : e;
+  double ang = (2.0 * M_PI * (double)k) / (double)Mt;
+  *c = cos(ang);
+  *s = -sin(ang);
+}
+
+// Two-level table of W_Mt: lo[l] = W^l (l < 2^bits), hi[h] = W^(h 2^bits).
+template <typename T>
+std::vector<T> build_two_level(int64_t Mt, int bits, int* lo_n, int* hi_n) {
+  *lo_n = 1 << bits;
+  *hi_n = (int)((Mt + *lo_n - 1) >> bits);
+  std::vector<T> t((size_t)2 * (*lo_n + *hi_n));
+  for (int l = 0; l < *lo_n; ++l) {
+    double c, s;
+    root_of_unity(l, Mt, &c, &s);
+    t[2 * l] = (T)c;
+    t[2 * l + 1] = (T)s;
+  }
+  for (int h = 0; h < *hi_n; ++h) {
+    double c, s;
+    root_of_unity((int64_t)h << bits, Mt, &c, &s);
+    t[2 * (*lo_n + h)] = (T)c;
+    t[2 * (*lo_n + h) + 1] = (T)s;
+  }
+  return t;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return ADFFT_OK;
+  if (e == cudaErrorMemoryAllocation) return ADFFT_ERR_OOM;
+  return ADFFT_ERR_CUDA;
+}
+
+// Configure the fused fold+FFT path; returns ADFFT_OK or a reason it does not apply.
+int setup_fold(Plan& p) {
+  FusedLaunch& L = p.fused;
+  int mode;
+  int64_t Nc, Mc;
+  if (!p.real) {
+    mode = kLoadComplex;
+    Nc = p.N;
+    Mc = p.M;
+  } else if (p.N % 2 == 0 && p.M % 2 == 0) {
+    mode = kLoadRealPacked;
+    Nc = p.N / 2;
+    Mc = p.M / 2;
+  } else {
+    mode = kLoadRealPlain;
+    Nc = p.N;
+    Mc = p.M;
+  }
+  const int64_t Np = gcd64(Mc, Nc);
+  const int64_t P = Mc / Np, q = Nc / Np;
+  if (!is_pow2(Np)) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  if (q > kMaxFold) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  const int64_t Mt = (mode == kLoadRealPacked) ? p.M : Mc;
+  if (Mt >= (int64_t(1) << 31)) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  const size_t esz = p.dbl ? 16 : 8;
+  const int vpt = fused_values_per_thread(p.dbl);
+  const int max_vals = vpt * kMaxThreads;
+
+  const int bits = (ilog2(Mt) + 1) / 2;
+  int lo_n, hi_n;
+  const int tw_n = (1 << bits) + (int)((Mt + (1 << bits) - 1) >> bits);
+  const int64_t region = Np + Np / 16 + 2;
+  int C = -1;
+  size_t smem = 0;
+  for (int c = 1; c <= std::min<int64_t>(P, kMaxCluster); ++c) {
+    if (P % c) continue;
+    const int64_t rpc = P / c;
+    if (rpc * Np > max_vals) continue;
+    const size_t bytes = ((size_t)((tw_n + 1) & ~1) + (size_t)(rpc * region)) * esz;
+    if (bytes > kSmemLimit) continue;
+    C = c;
+    smem = bytes;
+    break;
+  }
+  if (C < 0) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  const int64_t RPC = P / C;
+
+  FusedArgs& a = L.args;
+  memset(&a, 0, sizeof(a));
+  a.batch = p.batch;
+  a.in_stride = (mode == kLoadComplex) ? p.N : p.N;   // complex elements or real scalars per signal
+  a.M = p.M;
+  a.Np = (int)Np;
+  a.logNp = ilog2(Np);
+  a.P = (int)P;
+  a.q = (int)q;
+  a.RPC = (int)RPC;
+  a.C = C;
+  a.Nc = (int)Nc;
+  a.Mc = (int)Mc;
+  a.Mt = (int)Mt;
+  a.tw_bits = bits;
+  a.scale = p.scale;
+  a.region = (int)region;
+  // radices: the remainder (2, 4 or 8) first, then radix 16
+  // passes: a first pass of radix R0 = 2^(log2 Np mod 4) (16 if that is 0), then radix 16
+  const int L2 = a.logNp;
+  int lr0 = (L2 == 0) ? 0 : (L2 % 4 ? L2 % 4 : 4);
+  a.nrad = 1 + (L2 - lr0) / 4;
+  L.r0 = 1 << lr0;
+  a.divP = make_fastdiv((uint32_t)P);
+  a.divRPC = make_fastdiv((uint32_t)RPC);
+
+  // tables
+  size_t tw_bytes;
+  std::vector<unsigned char> host;
+  if (p.dbl) {
+    auto t = build_two_level<double>(Mt, bits, &lo_n, &hi_n);
+    tw_bytes = t.size() * sizeof(double);
+    host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + tw_bytes);
+  } else {
+    auto t = build_two_level<float>(Mt, bits, &lo_n, &hi_n);
+    tw_bytes = t.size() * sizeof(float);
+    host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + tw_bytes);
+  }
+  a.tw_lo_n = lo_n;
+  a.tw_hi_n = hi_n;
+  cudaError_t e = cudaMalloc(&p.d_tw, tw_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p.d_tw = nullptr;
+    return cuda_status(e);
+  }
+  e = cudaMemcpy(p.d_tw, host.data(), tw_bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e);
+  a.tw = p.d_tw;
+
+  int threads = (int)((RPC * Np + vpt - 1) / vpt);
+  threads = std::max(32, (threads + 31) / 32 * 32);
+  L.mode = mode;
+  L.dbl = p.dbl;
+  L.threads = threads;
+  L.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(p.batch, 65535));
+  L.smem = smem;
+  e = fused_prepare(L);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  if (C > 1 && fused_max_active_clusters(L) < 1) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  p.fold_ok = true;
+  return ADFFT_OK;
+}
+
+void release(Plan& p) {
+  if (p.d_tw) cudaFree(p.d_tw);
+  if (p.d_stage_in) cudaFree(p.d_stage_in);
+  if (p.d_stage_out) cudaFree(p.d_stage_out);
+  p.d_tw = p.d_stage_in = p.d_stage_out = nullptr;
+}
+
+adfft_plan_t fail(int code, adfft_plan_s* h) {
+  if (h) {
+    release(h->p);
+    delete h;
+  }
+  g_last_error = code;
+  return nullptr;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return na && nb && x < y + nb && y < x + na;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+}  // namespace adfft
+
+using adfft::Plan;
+
+extern "C" {
+
+const char* adfft_status_string(int s) {
+  switch (s) {
+    case ADFFT_OK: return "ADFFT_OK";
+    case ADFFT_ERR_INVALID_ARG: return "ADFFT_ERR_INVALID_ARG";
+    case ADFFT_ERR_INVALID_ALPHA: return "ADFFT_ERR_INVALID_ALPHA";
+    case ADFFT_ERR_UNSUPPORTED_SIZE: return "ADFFT_ERR_UNSUPPORTED_SIZE";
+    case ADFFT_ERR_MISALIGNED: return "ADFFT_ERR_MISALIGNED";
+    case ADFFT_ERR_OVERLAP: return "ADFFT_ERR_OVERLAP";
+    case ADFFT_ERR_CUDA: return "ADFFT_ERR_CUDA";
+    case ADFFT_ERR_OOM: return "ADFFT_ERR_OOM";
+    case ADFFT_ERR_TIMEOUT: return "ADFFT_ERR_TIMEOUT";
+    case ADFFT_ERR_NOT_SUPPORTED: return "ADFFT_ERR_NOT_SUPPORTED";
+    default: return "ADFFT_ERR_UNKNOWN";
+  }
+}
+
+int adfft_last_error(void) { return adfft::g_last_error; }
+
+adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dtype) {
+  using namespace adfft;
+  if (N < 1 || batch < 0 || dtype < ADFFT_R32 || dtype > ADFFT_C128) return fail(ADFFT_ERR_INVALID_ARG, nullptr);
+  if (M < 1) return fail(ADFFT_ERR_INVALID_ALPHA, nullptr);
+  if (N > (int64_t(1) << 40) || M > (int64_t(1) << 40)) return fail(ADFFT_ERR_UNSUPPORTED_SIZE, nullptr);
+  adfft_plan_s* h = new (std::nothrow) adfft_plan_s;
+  if (!h) return fail(ADFFT_ERR_OOM, nullptr);
+  Plan& p = h->p;
+  p.N = N;
+  p.M = M;
+  p.batch = batch;
+  p.dtype = dtype;
+  p.real = (dtype == ADFFT_R32 || dtype == ADFFT_R64);
+  p.dbl = (dtype == ADFFT_R64 || dtype == ADFFT_C128);
+  p.in_elem = p.real ? (p.dbl ? 8 : 4) : (p.dbl ? 16 : 8);
+  p.out_elem = p.dbl ? 16 : 8;
+  p.scale = 1.0 / (double)N;
+  if (cudaGetDevice(&p.device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ADFFT_ERR_CUDA, h);
+  }
+  int rc = setup_fold(p);
+  if (rc == ADFFT_OK) {
+    p.algo = ADFFT_ALGO_FOLD;
+  } else {
+    return fail(rc, h);
+  }
+  g_last_error = ADFFT_OK;
+  return h;
+}
+
+adfft_plan_t adfft_plan_create(int64_t N, double alpha, int64_t batch, int dtype) {
+  if (!(alpha > 0.0) || !isfinite(alpha)) return adfft::fail(ADFFT_ERR_INVALID_ALPHA, nullptr);
+  if (N < 1) return adfft::fail(ADFFT_ERR_INVALID_ARG, nullptr);
+  const double Md = alpha * (double)N;
+  if (!(Md < 9.0e15)) return adfft::fail(ADFFT_ERR_UNSUPPORTED_SIZE, nullptr);
+  const double Mr = nearbyint(Md);
+  if (fabs(Md - Mr) > 1e-9 * Md || Mr < 1.0) return adfft::fail(ADFFT_ERR_INVALID_ALPHA, nullptr);
+  return adfft_plan_create_bins(N, (int64_t)Mr, batch, dtype);
+}
+
+adfft_plan_t adfft_plan_create_ragged(const int64_t* N, const double* alpha, int64_t count, int dtype) {
+  (void)N;
+  (void)alpha;
+  (void)count;
+  (void)dtype;
+  return adfft::fail(ADFFT_ERR_NOT_SUPPORTED, nullptr);
+}
+
+int adfft_plan_offsets(adfft_plan_t plan, int64_t* in_off, int64_t* out_off) {
+  if (!plan) return ADFFT_ERR_INVALID_ARG;
+  const Plan& p = plan->p;
+  for (int64_t i = 0; i <= p.batch; ++i) {
+    if (in_off) in_off[i] = i * p.N;
+    if (out_off) out_off[i] = i * p.M;
+  }
+  return ADFFT_OK;
+}
+
+int adfft_plan_destroy(adfft_plan_t plan) {
+  if (!plan) return ADFFT_OK;
+  cudaDeviceSynchronize();
+  cudaGetLastError();
+  adfft::release(plan->p);
+  delete plan;
+  return ADFFT_OK;
+}
+
+int adfft_plan_set_scale(adfft_plan_t plan, double S) {
+  if (!plan || !isfinite(S)) return ADFFT_ERR_INVALID_ARG;
+  plan->p.scale = S;
+  plan->p.fused.args.scale = S;
+  return ADFFT_OK;
+}
+
+int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
+  if (!plan) return ADFFT_ERR_INVALID_ARG;
+  if (algo == ADFFT_ALGO_AUTO || algo == ADFFT_ALGO_FOLD) {
+    if (!plan->p.fold_ok) return ADFFT_ERR_NOT_SUPPORTED;
+    plan->p.algo = ADFFT_ALGO_FOLD;
+    return ADFFT_OK;
+  }
+  if (algo == ADFFT_ALGO_BLUESTEIN) return ADFFT_ERR_NOT_SUPPORTED;
+  return ADFFT_ERR_INVALID_ARG;
+}
+
+int adfft_plan_set_precision(adfft_plan_t plan, int mode) {
+  if (!plan) return ADFFT_ERR_INVALID_ARG;
+  if (mode == ADFFT_PREC_NATIVE) {
+    plan->p.precision = mode;
+    return ADFFT_OK;
+  }
+  if (mode == ADFFT_PREC_FP16X2 || mode == ADFFT_PREC_BF16X3) return ADFFT_ERR_NOT_SUPPORTED;
+  return ADFFT_ERR_INVALID_ARG;
+}
+
+int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
+  if (!plan || !info) return ADFFT_ERR_INVALID_ARG;
+  const Plan& p = plan->p;
+  memset(info, 0, sizeof(*info));
+  info->N = p.N;
+  info->M = p.M;
+  info->batch = p.batch;
+  info->dtype = p.dtype;
+  info->algo = p.algo;
+  info->fft_len = p.fused.args.Np;
+  info->residues = p.fused.args.P;
+  info->fold = p.fused.args.q;
+  info->cluster = p.fused.args.C;
+  info->passes = 1;
+  info->scale = p.scale;
+  return ADFFT_OK;
+}
+
+size_t adfft_plan_workspace_bytes(adfft_plan_t plan) {
+  (void)plan;
+  return 0;
+}
+
+int adfft_execute(adfft_plan_t plan, const void* d_in, void* d_out, void* stream) {
+  using namespace adfft;
+  if (!plan || !d_in || !d_out) return ADFFT_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  if (!aligned16(d_in) || !aligned16(d_out)) return ADFFT_ERR_MISALIGNED;
+  if (overlaps(d_in, p.in_bytes(), d_out, p.out_bytes())) return ADFFT_ERR_OVERLAP;
+  if (p.batch == 0) return ADFFT_OK;
+  cudaError_t e = fused_launch(p.fused, d_in, d_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  return ADFFT_OK;
+}
+
+int adfft_execute_adjoint(adfft_plan_t plan, const void* d_grad_out, void* d_grad_in, void* stream) {
+  (void)stream;
+  if (!plan || !d_grad_out || !d_grad_in) return ADFFT_ERR_INVALID_ARG;
+  return ADFFT_ERR_NOT_SUPPORTED;
+}
+
+int adfft_execute_host(adfft_plan_t plan, const void* h_in, void* h_out, void* stream) {
+  using namespace adfft;
+  if (!plan || !h_in || !h_out) return ADFFT_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ib = p.in_bytes(), ob = p.out_bytes();
+  if (p.batch == 0) return ADFFT_OK;
+  if (!p.d_stage_in) {
+    cudaError_t e = cudaMalloc(&p.d_stage_in, ib);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p.d_stage_in = nullptr;
+      return cuda_status(e);
+    }
+  }
+  if (!p.d_stage_out) {
+    cudaError_t e = cudaMalloc(&p.d_stage_out, ob);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p.d_stage_out = nullptr;
+      return cuda_status(e);
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(p.d_stage_in, h_in, ib, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  int rc = adfft_execute(plan, p.d_stage_in, p.d_stage_out, stream);
+  if (rc != ADFFT_OK) return rc;
+  e = cudaMemcpyAsync(h_out, p.d_stage_out, ob, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+}  // extern "C"

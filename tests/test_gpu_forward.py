@@ -1,0 +1,188 @@
+"""GPU parity of the forward alpha-DFT (C ABI) against the FP64 oracle.
+
+Tolerance (relative RMS over the compared bins, per signal, gate on the max):
+FP32 forms 2e-6 * log2(M); FP64 forms 1e-12.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_16665_gb300 import adfft, signals
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    adfft.load()
+    return torch
+
+
+def tol_for(M, dbl):
+    return 1e-12 if dbl else 2e-6 * max(1.0, np.log2(M))
+
+
+def rel_rms_rows(got, ref):
+    num = np.linalg.norm(got - ref, axis=-1)
+    den = np.maximum(np.linalg.norm(ref, axis=-1), 1e-300)
+    return num / den
+
+
+def run_plan(torch, x_np, M, dtype_code, scale=None, algo=None):
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).to(dev)
+    B, N = x.shape
+    plan = adfft.Plan(N, batch=B, dtype=dtype_code, M=M)
+    if scale is not None:
+        plan.set_scale(scale)
+    if algo is not None:
+        plan.set_algorithm(algo)
+    out_t = torch.complex128 if dtype_code in (adfft.R64, adfft.C128) else torch.complex64
+    X = torch.empty((B, M), dtype=out_t, device=dev)
+    plan.execute(x.data_ptr(), X.data_ptr())
+    torch.cuda.synchronize()
+    return X.cpu().numpy(), plan
+
+
+def make_input(B, N, dtype_code, seed):
+    rng = np.random.default_rng(seed)
+    if dtype_code in (adfft.R32, adfft.R64):
+        x = rng.standard_normal((B, N))
+    else:
+        x = rng.standard_normal((B, N)) + 1j * rng.standard_normal((B, N))
+    return x.astype({adfft.R32: np.float32, adfft.R64: np.float64,
+                     adfft.C64: np.complex64, adfft.C128: np.complex128}[dtype_code])
+
+
+SIZES = [
+    # (N, M): integer, rational, alpha < 1, tiny, ragged-by-batch shapes
+    (1, 1), (1, 4), (2, 2), (2, 8), (4, 12), (8, 8), (16, 64), (32, 96), (64, 160),
+    (64, 240), (128, 64), (128, 48), (256, 2048), (512, 512), (1024, 4096),
+    (2048, 5120), (4096, 15360), (4096, 32768), (8192, 65536), (16384, 131072),
+]
+
+
+@pytest.mark.parametrize("dtype_code", [adfft.R32, adfft.C64, adfft.R64, adfft.C128])
+@pytest.mark.parametrize("N,M", SIZES)
+def test_forward_matches_oracle_all_bins(dtype_code, N, M):
+    torch = _torch()
+    dbl = dtype_code in (adfft.R64, adfft.C128)
+    if dtype_code == adfft.C128 and N >= 16384:
+        pytest.skip("complex128 sub-FFTs of 16384 points exceed one CTA's shared memory")
+    B = 3
+    x = make_input(B, N, dtype_code, seed=N * 7 + M)
+    got, plan = run_plan(torch, x, M, dtype_code)
+    if M * N > 3e8:
+        bins = np.unique(np.concatenate([np.arange(64), M - 1 - np.arange(64),
+                                         np.random.default_rng(M).integers(0, M, 2048)]))
+        ref = oracle.alpha_dft(x.astype(np.complex128), M, bins=bins)
+        got = got[:, bins]
+    else:
+        ref = oracle.alpha_dft(x.astype(np.complex128), M)
+    err = rel_rms_rows(got, ref).max()
+    assert err <= tol_for(M, dbl), (err, plan.info.fft_len, plan.info.residues, plan.info.cluster)
+
+
+def test_single_real_fp64_workload_all_bins():
+    """1 real fp64 signal, N = 1024, alpha = 4 (4096 bins): FP64 tolerance 1e-12."""
+    torch = _torch()
+    x, _ = signals.single_r64()
+    got, _ = run_plan(torch, x, 4096, adfft.R64)
+    ref = oracle.alpha_dft(x, 4096)
+    assert rel_rms_rows(got, ref).max() <= 1e-12
+
+
+def test_scale_setting():
+    torch = _torch()
+    x = make_input(2, 256, adfft.C64, 5)
+    got, _ = run_plan(torch, x, 1024, adfft.C64, scale=1.0)
+    ref = oracle.alpha_dft(x.astype(np.complex128), 1024, S=1.0)
+    assert rel_rms_rows(got, ref).max() <= tol_for(1024, False)
+
+
+def test_batch_zero_is_a_no_op():
+    torch = _torch()
+    plan = adfft.Plan(64, batch=0, dtype=adfft.R32, M=256)
+    a = torch.empty(16, device="cuda")
+    b = torch.empty(16, device="cuda")
+    plan.execute(a.data_ptr(), b.data_ptr())
+
+
+def test_execute_rejects_bad_pointers():
+    torch = _torch()
+    plan = adfft.Plan(64, batch=2, dtype=adfft.R32, M=256)
+    x = torch.zeros(2 * 64 + 8, device="cuda")
+    X = torch.zeros(2 * 256 * 2 + 8, device="cuda")
+    with pytest.raises(adfft.AdfftError) as e:
+        plan.execute(x.data_ptr() + 4, X.data_ptr())
+    assert e.value.code == -4
+    with pytest.raises(adfft.AdfftError) as e:
+        plan.execute(X.data_ptr(), X.data_ptr() + 64)
+    assert e.value.code == -5
+    with pytest.raises(adfft.AdfftError) as e:
+        plan.execute(0, X.data_ptr())
+    assert e.value.code == -1
+
+
+def test_execute_host_matches_device_path():
+    torch = _torch()
+    x = make_input(4, 1024, adfft.R32, 11)
+    dev_out, plan = run_plan(torch, x, 8192, adfft.R32)
+    hx = torch.from_numpy(x).pin_memory()
+    hX = torch.empty((4, 8192), dtype=torch.complex64).pin_memory()
+    plan.execute_host(hx.data_ptr(), hX.data_ptr())
+    assert np.array_equal(hX.numpy(), dev_out)
+
+
+def test_tone_on_fine_grid_gpu():
+    """A tone at j/(alpha T): X_j = T A and the bins j + k alpha vanish (closed form)."""
+    torch = _torch()
+    N, alpha, j, A = 4096, 8, 1234 * 8 + 3, 0.75
+    n = np.arange(N)
+    x = (A * np.exp(2j * np.pi * (j / alpha) * n / N)).astype(np.complex128)[None]
+    got, _ = run_plan(torch, x, alpha * N, adfft.C128)
+    assert abs(got[0, j] - A) < 1e-12
+    same = np.arange(j % alpha, alpha * N, alpha)
+    same = same[same != j]
+    assert np.max(np.abs(got[0, same])) < 1e-12
+
+
+@pytest.mark.parametrize("alpha", [2.5, 3.75])
+def test_complex_rational_alpha_workload(alpha):
+    """Complex64 signals, N = 8192, alpha in {2.5, 3.75}: sampled bins of 8 signals."""
+    torch = _torch()
+    x, _ = signals.batch_c64(batch=8, alpha=alpha)
+    M = int(round(alpha * 8192))
+    got, _ = run_plan(torch, x, M, adfft.C64)
+    rng = np.random.default_rng(3)
+    bins = np.unique(np.concatenate([np.arange(32), M - 1 - np.arange(32), rng.integers(0, M, 3000)]))
+    ref = oracle.alpha_dft(x.astype(np.complex128), M, bins=bins)
+    assert rel_rms_rows(got[:, bins], ref).max() <= tol_for(M, False)
+
+
+def test_batch_real_fp32_full_size_sampled():
+    """4096 real fp32 signals, N = 16384, alpha = 8, in the benchmark's launch
+    configuration; 24 signals checked on 1500 sampled bins each."""
+    torch = _torch()
+    B, N, alpha = 4096, 16384, 8
+    M = alpha * N
+    x, _ = signals.batch_r32(batch=B, N=N, alpha=alpha)
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(x).to(dev)
+    plan = adfft.Plan(N, batch=B, dtype=adfft.R32, M=M)
+    X = torch.empty((B, M), dtype=torch.complex64, device=dev)
+    plan.execute(xt.data_ptr(), X.data_ptr())
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    sigs = np.unique(np.concatenate([[0, B - 1], rng.integers(0, B, 22)]))
+    bins = np.unique(np.concatenate([[0, 1, M // 2, M - 1], rng.integers(0, M, 1500)]))
+    got = X[torch.from_numpy(sigs).to(dev)][:, torch.from_numpy(bins).to(dev)].cpu().numpy()
+    ref = oracle.alpha_dft(x[sigs].astype(np.float64), M, bins=bins)
+    err = rel_rms_rows(got, ref)
+    assert err.max() <= tol_for(M, False), err.max()
+    # a property that holds at every bin: Hermitian symmetry of a real signal's spectrum
+    Xs = X[torch.from_numpy(sigs[:4]).to(dev)].cpu().numpy()
+    m = np.arange(1, M)
+    assert np.max(np.abs(Xs[:, M - m] - np.conj(Xs[:, m]))) <= 1e-6 * np.max(np.abs(Xs))
