@@ -175,11 +175,22 @@ int adfft_execute_adjoint(adfft_plan_t plan, const void *d_grad_out, void *d_gra
                           void *stream);
 
 /*
+ * Synchronise `stream`, then read and clear the plan's device status word.
+ * Returns ADFFT_OK, or ADFFT_ERR_TIMEOUT if a kernel of the plan gave up a
+ * bounded device-side wait (for example on an asynchronous copy) since the
+ * last call; the outputs of the launches concerned are then invalid.  Kernels
+ * never trap or spin without limit: a wait that runs out sets this word and
+ * the kernel returns.
+ */
+int adfft_plan_sync_status(adfft_plan_t plan, void *stream);
+
+/*
  * End-to-end forward transform from HOST memory: copies h_in to the device,
  * runs adfft_execute, copies the spectrum back to h_out and synchronises the
  * stream.  The device staging buffers are allocated by the plan on first use
  * and kept until adfft_plan_destroy.  Host buffers should be page-locked for
- * full copy bandwidth.
+ * full copy bandwidth.  Returns after the stream is synchronised, with the
+ * plan's status word checked as by adfft_plan_sync_status.
  */
 int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *stream);
 

@@ -33,7 +33,7 @@ EXPORTS = (
     "adfft_plan_offsets", "adfft_last_error", "adfft_status_string", "adfft_plan_destroy",
     "adfft_plan_set_scale", "adfft_plan_set_algorithm", "adfft_plan_set_precision",
     "adfft_plan_get_info", "adfft_plan_workspace_bytes", "adfft_execute",
-    "adfft_execute_adjoint", "adfft_execute_host",
+    "adfft_execute_adjoint", "adfft_execute_host", "adfft_plan_sync_status",
 )
 
 
@@ -79,6 +79,7 @@ def load(path: str | None = None):
         "adfft_execute": ([vp, vp, vp, vp], i32),
         "adfft_execute_adjoint": ([vp, vp, vp, vp], i32),
         "adfft_execute_host": ([vp, vp, vp, vp], i32),
+        "adfft_plan_sync_status": ([vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -154,6 +155,11 @@ class Plan:
         _check(self.lib.adfft_execute_host(self._h, ctypes.c_void_p(h_in), ctypes.c_void_p(h_out),
                                            ctypes.c_void_p(_stream_handle(stream))),
                "adfft_execute_host")
+
+    def sync_status(self, stream=None):
+        """Synchronise the stream and raise if a kernel of the plan reported an error."""
+        _check(self.lib.adfft_plan_sync_status(self._h, ctypes.c_void_p(_stream_handle(stream))),
+               "adfft_plan_sync_status")
 
     def destroy(self):
         if self._h is not None and self._h.value:

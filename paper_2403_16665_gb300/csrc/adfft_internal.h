@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "../../include/adfft.h"
+#include "adfft.h"
 #include "fft_device.cuh"
 #include "fused.cuh"
 
@@ -37,6 +37,7 @@ struct Plan {
   bool fold_ok = false;
   FusedLaunch fused{};
   void* d_tw = nullptr;               // twiddle table of the fused path
+  int* d_status = nullptr;            // device status word (0, or ADFFT_ERR_TIMEOUT)
 
   // host-memory staging of adfft_execute_host
   void* d_stage_in = nullptr;

@@ -12,11 +12,13 @@
 //   X_j = E_j + W_M^j O_j,  X_{j+Mc} = E_j - W_M^j O_j,  X_{M-j} = conj X_j.
 //
 // One cluster of C CTAs owns one signal at a time; CTA c holds residues
-// [c*RPC, (c+1)*RPC) of it in shared memory.  Pass 1 (K1) folds and twiddles
-// the input straight from global memory into its first radix-R butterfly;
-// the remaining Stockham passes (K2) run in shared memory; the epilogue (K3)
-// gathers U across the cluster through distributed shared memory so that each
-// CTA writes a contiguous, coalesced range of output bins in natural order.
+// [c*RPC, (c+1)*RPC) of it in shared memory.  The signal's input is brought
+// into shared memory by a bulk (TMA) copy issued while the previous signal is
+// still being transformed.  Pass 1 (K1) folds and twiddles the staged input
+// into its first radix-R butterfly; the remaining radix-16 Stockham passes
+// (K2) run in shared memory; the epilogue (K3) gathers U across the cluster
+// through distributed shared memory so that each CTA writes a contiguous,
+// coalesced range of output bins in natural order.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -34,6 +36,9 @@ enum LoadMode : int {
   kLoadRealPlain = 2     // real input read as complex with zero imaginary part (odd N or odd M)
 };
 
+// Status word values written by kernels (0 = no error).
+constexpr int kStatusTimeout = -8;
+
 struct FusedArgs {
   const void* in;
   void* out;
@@ -50,75 +55,100 @@ struct FusedArgs {
   double scale;
   int region;            // complex elements per residue region in shared memory
   int nrad;              // passes: one of radix R0 (template argument), nrad-1 of radix 16
+  int stage_bytes;       // > 0: each signal's input is bulk-copied into shared memory first
+  int* status;           // device status word of the plan
   FastDiv divP, divRPC;
 };
 
+// Shared-memory layout of the fused kernel (byte offsets).
+struct FusedSmem {
+  int tw, stage, buf, total;
+};
+__host__ __device__ inline FusedSmem fused_smem_layout(int tw_n, int stage_bytes, int rpc, int region,
+                                                       int esz) {
+  FusedSmem s;
+  s.tw = 16;                                         // [0, 16): the mbarrier
+  s.stage = s.tw + ((tw_n * esz + 15) & ~15);
+  s.buf = s.stage + ((stage_bytes + 15) & ~15);
+  s.total = s.buf + rpc * region * esz;
+  return s;
+}
+
 template <typename V>
-__device__ __forceinline__ V ld_in(const void* base, long long idx, int mode) {
+__device__ __forceinline__ V ld_u(const void* base, int idx, int mode, bool smem) {
   using R = typename real_of<V>::type;
+  if (smem) {
+    if (mode == kLoadRealPlain) return cmake<V>(reinterpret_cast<const R*>(base)[idx], (R)0);
+    return reinterpret_cast<const V*>(base)[idx];
+  }
   if (mode == kLoadRealPlain) return cmake<V>(__ldg(reinterpret_cast<const R*>(base) + idx), (R)0);
   return __ldg(reinterpret_cast<const V*>(base) + idx);
 }
 
-// Twiddles W_{Ns R}^{k i}, i = 1..R-1, applied to v[i] from one table lookup of
-// w = W^k: w^(2h) = w^h * w^h, w^(h+l) = w^h * w^l (h the highest power of two
-// below i), so no power is more than log2(R) + 1 products away from w.
-__host__ __device__ constexpr int high_pow2(int i) { return (i & (i - 1)) == 0 ? i / 2 : (i >= 8 ? 8 : i >= 4 ? 4 : 2); }
-
-template <int R, typename V, int i>
-__device__ __forceinline__ void twiddle_powers(V* w, std::integral_constant<int, i>) {
-  if constexpr (i < R) {
-    constexpr int h = high_pow2(i);
-    w[i] = cmul(w[h], w[i - h]);
-    twiddle_powers<R, V>(w, std::integral_constant<int, i + 1>());
-  }
-}
-
-template <int R, typename V>
-__device__ __forceinline__ void apply_stage_twiddles(V* v, V w1) {
+// Multiply v[n][i] (n < NI items, i = 1..R-1) by w^i, w = W^k from one table
+// lookup.  Powers are generated on the fly with few live registers:
+// w^2 = w w, w^3 = w^2 w, w^4 = w^2 w^2, w^(4b) = w^(4(b-1)) w^4 and
+// w^(4b+c) = w^(4b) w^c, so every power is at most five products from w.
+template <int R, int NI, typename V>
+__device__ __forceinline__ void apply_stage_twiddles(V (*v)[R], V w1) {
   if constexpr (R > 1) {
-    V w[R];
-    w[1] = w1;
-    twiddle_powers<R, V>(w, std::integral_constant<int, 2>());
+    const V w2 = cmul(w1, w1);
+    const V w3 = cmul(w2, w1);
+    const V w4 = cmul(w2, w2);
+    V wb = w4;
 #pragma unroll
-    for (int i = 1; i < R; ++i) v[i] = cmul(v[i], w[i]);
+    for (int i = 1; i < R; ++i) {
+      const int b = i >> 2, c = i & 3;
+      if (b >= 2 && c == 0) wb = cmul(wb, w4);
+      V wi;
+      if (b == 0) wi = (c == 1) ? w1 : (c == 2) ? w2 : w3;
+      else wi = (c == 0) ? wb : cmul(wb, (c == 1) ? w1 : (c == 2) ? w2 : w3);
+#pragma unroll
+      for (int n = 0; n < NI; ++n) v[n][i] = cmul(v[n][i], wi);
+    }
   }
 }
 
 // Pass 1 (Ns = 1): fold, residue twiddle and the first radix-R butterfly,
-// reading u from global memory and writing the CTA's residue regions.
+// reading u (staged in shared memory or straight from global memory) and
+// writing the CTA's residue regions.  Element n = j + i*Np/R + f*Np of residue r
+// is twiddled by W_Mt^{s r n} = W_Mt^{s r j} * c^i * g^f with the per-residue
+// constants c = W_Mt^{s r Np/R} and g = W_Mt^{s r Np} (s = Mt/Mc), so each
+// (j, r) costs one table lookup.
 template <int R, typename V>
-__device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, int mode, V* buf,
-                                           const TwTable<V>& tab, int r0) {
+__device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, int mode, bool staged,
+                                           V* buf, const TwTable<V>& tab, int r0) {
   const int items = a.Np / R;
   const unsigned T = blockDim.x;
   const unsigned Mt = (unsigned)a.Mt;
   const unsigned s = (unsigned)(a.Mt / a.Mc);
   for (int rl = 0; rl < a.RPC; ++rl) {
     const unsigned long long sr = (unsigned long long)s * (unsigned)(r0 + rl);
-    const unsigned d_i = (unsigned)((sr * (unsigned)items) % Mt);
-    const unsigned d_f = (unsigned)((sr * (unsigned)a.Np) % Mt);
+    const V c1 = tab((unsigned)((sr * (unsigned)items) % Mt));
+    const V g1 = tab((unsigned)((sr * (unsigned)a.Np) % Mt));
     const unsigned d_T = (unsigned)((sr * T) % Mt);
     unsigned e_j = (unsigned)((sr * threadIdx.x) % Mt);
     V* dst = buf + rl * a.region;
     for (int j = threadIdx.x; j < items; j += T) {
       V acc[R];
+      // fold: acc[i] = sum_f u[j + i items + f Np] g^f
 #pragma unroll
-      for (int i = 0; i < R; ++i) acc[i] = czero<V>();
-      unsigned e_f = e_j;
-      for (int f = 0; f < a.q; ++f) {
-        unsigned e = e_f;
-        const long long nb = (long long)j + (long long)f * a.Np;
+      for (int i = 0; i < R; ++i) acc[i] = ld_u<V>(u, j + i * items, mode, staged);
+      if (a.q > 1) {
+        V gf = g1;
+        for (int f = 1; f < a.q; ++f) {
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const V x = ld_in<V>(u, nb + (long long)i * items, mode);
-          const V w = tab(e);
-          acc[i] = cadd(acc[i], cmul(x, w));
-          e += d_i;
-          if (e >= Mt) e -= Mt;
+          for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_u<V>(u, j + i * items + f * a.Np, mode, staged), gf));
+          gf = cmul(gf, g1);
         }
-        e_f += d_f;
-        if (e_f >= Mt) e_f -= Mt;
+      }
+      // residue twiddle W^{s r j} c^i
+      V wi = tab(e_j);
+      acc[0] = cmul(acc[0], wi);
+#pragma unroll
+      for (int i = 1; i < R; ++i) {
+        wi = cmul(wi, c1);
+        acc[i] = cmul(acc[i], wi);
       }
       DFT<R, V>::run(acc);
 #pragma unroll
@@ -131,7 +161,9 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, in
 
 // One in-place Stockham pass of radix R over all residue regions of the CTA.
 // Item (rl, j): reads elements j + i*Np/R, twiddles by W_{Ns R}^{(j mod Ns) i},
-// runs DFT_R and writes to (j / Ns) * Ns * R + (j mod Ns) + i*Ns.
+// runs DFT_R and writes to (j / Ns) * Ns * R + (j mod Ns) + i*Ns.  When the
+// block size is a multiple of Np/R every item of a thread has the same j, and
+// the twiddles are computed once for all of its residues.
 template <int R, int VPT, typename V>
 __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const TwTable<V>& tab,
                                               int Ns, int logNs) {
@@ -141,80 +173,158 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
   const int items_res = 1 << log_items;
   const int items = a.RPC * items_res;
   const int T = blockDim.x;
+  const bool same_j = (T & (items_res - 1)) == 0;
   const unsigned tw_step = (unsigned)a.Mt / ((unsigned)Ns << LOGR);   // Mt / (Ns R)
+  // pad16(j + i*S) = pad16(j) + i*(S + S/16) for S a multiple of 16
+  const int in_step = items_res + (items_res >> 4);
   V v[IPT][R];
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
-    const int w = threadIdx.x + it * T;
-    if (w < items) {
-      const int rl = w >> log_items;
-      const int j = w & (items_res - 1);
-      const V* src = buf + rl * a.region;
+    const int wi = threadIdx.x + it * T;
+    const int rl = wi >> log_items;
+    const int j = wi & (items_res - 1);
+    const V* src = buf + rl * a.region;
+    if (items_res >= 16) {
+      const V* p0 = src + pad16(j);
 #pragma unroll
-      for (int i = 0; i < R; ++i) v[it][i] = src[pad16(j + (i << log_items))];
-      const int k = j & (Ns - 1);
-      if (k != 0) apply_stage_twiddles<R>(v[it], tab((unsigned)k * tw_step));
-      DFT<R, V>::run(v[it]);
+      for (int i = 0; i < R; ++i) v[it][i] = (wi < items) ? p0[i * in_step] : czero<V>();
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[it][i] = (wi < items) ? src[pad16(j + (i << log_items))] : czero<V>();
     }
   }
+  if (same_j) {
+    const int j = threadIdx.x & (items_res - 1);
+    apply_stage_twiddles<R, IPT>(v, tab((unsigned)(j & (Ns - 1)) * tw_step));
+  } else {
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int j = (threadIdx.x + it * T) & (items_res - 1);
+      apply_stage_twiddles<R, 1>(&v[it], tab((unsigned)(j & (Ns - 1)) * tw_step));
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) DFT<R, V>::run(v[it]);
   __syncthreads();
+  const int out_step = Ns + (Ns >> 4);
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
-    const int w = threadIdx.x + it * T;
-    if (w < items) {
-      const int rl = w >> log_items;
-      const int j = w & (items_res - 1);
+    const int wi = threadIdx.x + it * T;
+    if (wi < items) {
+      const int rl = wi >> log_items;
+      const int j = wi & (items_res - 1);
       const int k = j & (Ns - 1);
       const int base = ((j >> logNs) << (logNs + LOGR)) + k;
       V* dst = buf + rl * a.region;
+      if (Ns >= 16) {
+        V* p0 = dst + pad16(base);
 #pragma unroll
-      for (int i = 0; i < R; ++i) dst[pad16(base + i * Ns)] = v[it][i];
+        for (int i = 0; i < R; ++i) p0[i * out_step] = v[it][i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) dst[pad16(base + i * Ns)] = v[it][i];
+      }
     }
   }
   __syncthreads();
 }
 
-// Address of U_idx (0 <= idx < Mc) in the cluster's shared memory.
-template <typename V>
-__device__ __forceinline__ const V* u_addr(const FusedArgs& a, const V* buf, unsigned idx,
-                                           cg::cluster_group& cluster) {
-  const unsigned k = fdiv(idx, a.divP);
-  const unsigned r = idx - k * (unsigned)a.P;
-  const unsigned owner = fdiv(r, a.divRPC);
-  const unsigned rl = r - owner * (unsigned)a.RPC;
-  const V* p = buf + rl * a.region + pad16((int)k);
-  if (a.C > 1) return cluster.map_shared_rank(p, owner);
-  return p;
-}
+// independent U loads in flight per thread in the epilogue (bounded by registers)
+template <typename V, int MODE>
+constexpr int epilogue_unroll() { return sizeof(V) == 16 ? 4 : (MODE == kLoadRealPacked ? 6 : 8); }
 
 // R0: radix of the first pass (1, 2, 4, 8 or 16); every later pass is radix 16.
 template <typename V, int MODE, int VPT, int R0>
 __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   using Rl = typename real_of<V>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tw_s = reinterpret_cast<V*>(smem_raw);
+  const int esz = (int)sizeof(V);
   const int tw_n = a.tw_lo_n + a.tw_hi_n;
-  V* buf = tw_s + ((tw_n + 1) & ~1);
+  const FusedSmem L = fused_smem_layout(tw_n, a.stage_bytes, a.RPC, a.region, esz);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  V* tw_s = reinterpret_cast<V*>(smem_raw + L.tw);
+  unsigned char* stage = smem_raw + L.stage;
+  V* buf = reinterpret_cast<V*>(smem_raw + L.buf);
+  const bool staged = a.stage_bytes > 0;
+
+  if (threadIdx.x == 0 && staged) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
   for (int i = threadIdx.x; i < tw_n; i += blockDim.x) tw_s[i] = reinterpret_cast<const V*>(a.tw)[i];
   __syncthreads();
   TwTable<V> tab{tw_s, tw_s + a.tw_lo_n, a.tw_bits, (1u << a.tw_bits) - 1u};
 
   cg::cluster_group cluster = cg::this_cluster();
   const int c = (int)blockIdx.x;          // rank within the cluster (grid.x == C)
+
+  // Epilogue work split: CTA c writes bins j in [c*per, (c+1)*per) (real packed
+  // input: j <= Mc/2 and their mirrors), per a multiple of P.  Thread t keeps the
+  // residue r_l = t mod P for every j it handles (T' = P * floor(T/P) threads
+  // take part), so its shared-memory sources are fixed for the whole kernel.
+  const unsigned P = (unsigned)a.P;
+  const unsigned Tp = (blockDim.x / P) * P;
+  const bool lane_ok = threadIdx.x < Tp;
+  const unsigned r_l = threadIdx.x % P;
+  const unsigned k_step = Tp / P;
+  const unsigned jtot = (MODE == kLoadRealPacked) ? (unsigned)a.Mc / 2 + 1 : (unsigned)a.Mc;
+  const unsigned per = ((jtot + a.C - 1) / a.C + P - 1) / P * P;
+  const unsigned j_first = c * per;
+  const unsigned j_last = min(jtot, j_first + per) - 1;      // inclusive
+  const unsigned k_first = j_first / P + threadIdx.x / P;
+  const V* base_u;
+  const V* base_p;
+  {
+    const unsigned rp = (P - r_l) % P;                        // residue of the mirror bin Mc - j
+    const unsigned ou = r_l / (unsigned)a.RPC, op = rp / (unsigned)a.RPC;
+    const V* lu = buf + (r_l - ou * a.RPC) * a.region;
+    const V* lp = buf + (rp - op * a.RPC) * a.region;
+    base_u = (a.C > 1) ? cluster.map_shared_rank(lu, ou) : lu;
+    base_p = (a.C > 1) ? cluster.map_shared_rank(lp, op) : lp;
+  }
   const int r0 = c * a.RPC;
-  const unsigned T = blockDim.x;
   const Rl S = (Rl)a.scale;
   constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : 4;
+  constexpr int kEpilogueUnroll = epilogue_unroll<V, MODE>();
+  const size_t in_bytes_per_sig = (MODE == kLoadComplex ? sizeof(V) : sizeof(Rl)) * (size_t)a.in_stride;
+  uint32_t phase = 0, fail_phase = 0;
+  bool failed = false;
+
+  // prefetch the first signal's input
+  if (staged && threadIdx.x == 0 && (long long)blockIdx.y < a.batch) {
+    mbar_arrive_expect_tx(bar, (uint32_t)a.stage_bytes);
+    bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + blockIdx.y * in_bytes_per_sig,
+                  (uint32_t)a.stage_bytes, bar);
+  }
 
   for (long long sig = blockIdx.y; sig < a.batch; sig += gridDim.y) {
     const void* u;
-    if (MODE == kLoadComplex) u = reinterpret_cast<const V*>(a.in) + sig * a.in_stride;
-    else u = reinterpret_cast<const Rl*>(a.in) + sig * a.in_stride;
+    if (staged) {
+      u = stage;
+      if (!failed && !mbar_wait_bounded(bar, phase)) {
+        failed = true;
+        fail_phase = phase;
+        if (a.status) atomicExch(a.status, kStatusTimeout);
+      }
+      phase ^= 1u;
+    } else {
+      u = reinterpret_cast<const unsigned char*>(a.in) + sig * in_bytes_per_sig;
+    }
     V* out = reinterpret_cast<V*>(a.out) + sig * a.M;
 
     // ---- K1: fold + residue twiddle + first radix
-    first_pass<R0, V>(a, u, MODE, buf, tab, r0);
+    if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
+    first_pass<R0, V>(a, u, MODE, staged, buf, tab, r0);
     __syncthreads();
+
+    // prefetch the next signal's input while this one is transformed
+    const long long nxt = sig + gridDim.y;
+    if (staged && threadIdx.x == 0 && nxt < a.batch && !failed) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(bar, (uint32_t)a.stage_bytes);
+      bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + nxt * in_bytes_per_sig,
+                    (uint32_t)a.stage_bytes, bar);
+    }
 
     // ---- K2: radix-16 Stockham passes in shared memory
     int Ns = R0, logNs = LOGR0;
@@ -225,38 +335,66 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     }
 
     // ---- K3: interleave epilogue through distributed shared memory
-    if (a.C > 1) cluster.sync(); else __syncthreads();
-    if (MODE == kLoadRealPacked) {
-      const unsigned Mc = (unsigned)a.Mc;
-      const unsigned total = Mc / 2 + 1;
-      const unsigned per = (total + a.C - 1) / a.C;
-      const unsigned j0 = c * per;
-      const unsigned j1 = min(total, j0 + per);
-      for (unsigned j = j0 + threadIdx.x; j < j1; j += T) {
-        const unsigned jp = (j == 0) ? 0u : Mc - j;
-        const V Uj = *u_addr<V>(a, buf, j, cluster);
-        const V Ujp = *u_addr<V>(a, buf, jp, cluster);
-        const V E = cscale(cadd(Uj, cconj(Ujp)), (Rl)0.5);
-        const V O = cscale(cmul_mi(csub(Uj, cconj(Ujp))), (Rl)0.5);
-        const V wO = cmul(tab(j), O);
-        const V X1 = cscale(cadd(E, wO), S);
-        const V X2 = cscale(csub(E, wO), S);
-        out[j] = X1;
-        out[j + Mc] = X2;
-        if (j != 0 && 2 * j != Mc) {
-          out[Mc - j] = cconj(X2);
-          out[(unsigned long long)a.M - j] = cconj(X1);
+    if (a.C > 1) { cluster_arrive(); cluster_wait(); } else { __syncthreads(); }
+    if (lane_ok) {
+      if (MODE == kLoadRealPacked) {
+        const unsigned Mc = (unsigned)a.Mc;
+        const unsigned half = Mc / 2;
+        for (unsigned kb = k_first; kb * P + r_l <= min(half, j_last); kb += k_step * kEpilogueUnroll) {
+          V Ua[kEpilogueUnroll], Ub[kEpilogueUnroll];
+#pragma unroll
+          for (int e = 0; e < kEpilogueUnroll; ++e) {
+            const unsigned k = kb + e * k_step;
+            const unsigned j = k * P + r_l;
+            if (j <= half && j <= j_last) {
+              const unsigned kp = (r_l == 0) ? ((unsigned)a.Np - k) & ((unsigned)a.Np - 1) : (unsigned)a.Np - 1 - k;
+              Ua[e] = base_u[pad16((int)k)];
+              Ub[e] = base_p[pad16((int)kp)];
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < kEpilogueUnroll; ++e) {
+            const unsigned k = kb + e * k_step;
+            const unsigned j = k * P + r_l;
+            if (j <= half && j <= j_last) {
+              const V E = cscale(cadd(Ua[e], cconj(Ub[e])), (Rl)0.5);
+              const V O = cscale(cmul_mi(csub(Ua[e], cconj(Ub[e]))), (Rl)0.5);
+              const V wO = cmul(tab(j), O);
+              const V X1 = cscale(cadd(E, wO), S);
+              const V X2 = cscale(csub(E, wO), S);
+              out[j] = X1;
+              out[j + Mc] = X2;
+              if (j != 0 && 2 * j != Mc) {
+                out[Mc - j] = cconj(X2);
+                out[(unsigned long long)a.M - j] = cconj(X1);
+              }
+            }
+          }
+        }
+      } else {
+        for (unsigned kb = k_first; kb * P + r_l <= j_last; kb += k_step * kEpilogueUnroll) {
+          V Ua[kEpilogueUnroll];
+#pragma unroll
+          for (int e = 0; e < kEpilogueUnroll; ++e) {
+            const unsigned k = kb + e * k_step;
+            if (k * P + r_l <= j_last) Ua[e] = base_u[pad16((int)k)];
+          }
+#pragma unroll
+          for (int e = 0; e < kEpilogueUnroll; ++e) {
+            const unsigned k = kb + e * k_step;
+            const unsigned m = k * P + r_l;
+            if (m <= j_last) out[m] = cscale(Ua[e], S);
+          }
         }
       }
-    } else {
-      const unsigned Mc = (unsigned)a.Mc;
-      const unsigned per = (Mc + a.C - 1) / a.C;
-      const unsigned m0 = c * per;
-      const unsigned m1 = min(Mc, m0 + per);
-      for (unsigned m = m0 + threadIdx.x; m < m1; m += T) out[m] = cscale(*u_addr<V>(a, buf, m, cluster), S);
     }
-    if (a.C > 1) cluster.sync(); else __syncthreads();
+    // this CTA has read what it needs from the cluster; the wait that pairs with
+    // this arrive comes before the next signal overwrites shared memory
+    if (a.C > 1) cluster_arrive(); else __syncthreads();
   }
+  if (a.C > 1 && (long long)blockIdx.y < a.batch) cluster_wait();
+  // a copy can only still be in flight after a timed-out wait: give it time to land
+  if (failed && threadIdx.x == 0) mbar_wait_bounded(bar, fail_phase);
 }
 
 }  // namespace adfft

@@ -108,17 +108,25 @@ int setup_fold(Plan& p) {
   int lo_n, hi_n;
   const int tw_n = (1 << bits) + (int)((Mt + (1 << bits) - 1) >> bits);
   const int64_t region = Np + Np / 16 + 2;
-  int C = -1;
+  // input bytes per signal; staged through shared memory by bulk copies when 16-byte granular
+  const int64_t sig_bytes = (int64_t)p.N * (int64_t)p.in_elem;
+  const bool can_stage = (sig_bytes % 16) == 0 && sig_bytes <= (int64_t)kSmemLimit;
+  int C = -1, stage = 0;
   size_t smem = 0;
-  for (int c = 1; c <= std::min<int64_t>(P, kMaxCluster); ++c) {
-    if (P % c) continue;
-    const int64_t rpc = P / c;
-    if (rpc * Np > max_vals) continue;
-    const size_t bytes = ((size_t)((tw_n + 1) & ~1) + (size_t)(rpc * region)) * esz;
-    if (bytes > kSmemLimit) continue;
-    C = c;
-    smem = bytes;
-    break;
+  for (int pass = 0; pass < 2 && C < 0; ++pass) {
+    const int st = (pass == 0 && can_stage) ? (int)sig_bytes : 0;
+    if (pass == 0 && !can_stage) continue;
+    for (int c = 1; c <= std::min<int64_t>(P, kMaxCluster); ++c) {
+      if (P % c) continue;
+      const int64_t rpc = P / c;
+      if (rpc * Np > max_vals) continue;
+      const FusedSmem lay = fused_smem_layout(tw_n, st, (int)rpc, (int)region, (int)esz);
+      if ((size_t)lay.total > kSmemLimit) continue;
+      C = c;
+      stage = st;
+      smem = (size_t)lay.total;
+      break;
+    }
   }
   if (C < 0) return ADFFT_ERR_UNSUPPORTED_SIZE;
   const int64_t RPC = P / C;
@@ -140,6 +148,8 @@ int setup_fold(Plan& p) {
   a.tw_bits = bits;
   a.scale = p.scale;
   a.region = (int)region;
+  a.stage_bytes = stage;
+  a.status = p.d_status;
   // radices: the remainder (2, 4 or 8) first, then radix 16
   // passes: a first pass of radix R0 = 2^(log2 Np mod 4) (16 if that is 0), then radix 16
   const int L2 = a.logNp;
@@ -191,6 +201,8 @@ int setup_fold(Plan& p) {
 }
 
 void release(Plan& p) {
+  if (p.d_status) cudaFree(p.d_status);
+  p.d_status = nullptr;
   if (p.d_tw) cudaFree(p.d_tw);
   if (p.d_stage_in) cudaFree(p.d_stage_in);
   if (p.d_stage_out) cudaFree(p.d_stage_out);
@@ -258,6 +270,14 @@ adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dty
   if (cudaGetDevice(&p.device) != cudaSuccess) {
     cudaGetLastError();
     return fail(ADFFT_ERR_CUDA, h);
+  }
+  {
+    cudaError_t e = cudaMalloc(&p.d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(cuda_status(e), h);
+    }
   }
   int rc = setup_fold(p);
   if (rc == ADFFT_OK) {
@@ -408,7 +428,26 @@ int adfft_execute_host(adfft_plan_t plan, const void* h_in, void* h_out, void* s
   e = cudaMemcpyAsync(h_out, p.d_stage_out, ob, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamSynchronize(s);
-  return cuda_status(e);
+  if (e != cudaSuccess) return cuda_status(e);
+  return adfft_plan_sync_status(plan, stream);
+}
+
+int adfft_plan_sync_status(adfft_plan_t plan, void* stream) {
+  using namespace adfft;
+  if (!plan) return ADFFT_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (h != 0) {
+    e = cudaMemsetAsync(p.d_status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    return h == kStatusTimeout ? ADFFT_ERR_TIMEOUT : ADFFT_ERR_CUDA;
+  }
+  return ADFFT_OK;
 }
 
 }  // extern "C"
