@@ -3,5 +3,6 @@
     from paper_2403_16665_gb300 import alpha_dft
     X = alpha_dft(x_cuda, alpha=8)      # X[b, m] = (1/N) sum_n x[b, n] exp(-2 pi i m n/(alpha N))
 """
+from .autograd import AlphaDFT, alpha_dft_autograd  # noqa: F401
 from .adfft import (ALGO_AUTO, ALGO_BLUESTEIN, ALGO_FOLD, C64, C128, PREC_BF16X3,  # noqa: F401
                     PREC_FP16X2, PREC_NATIVE, R32, R64, AdfftError, Plan, alpha_dft, load)

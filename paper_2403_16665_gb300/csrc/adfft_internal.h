@@ -54,6 +54,12 @@ struct Plan {
 cudaError_t fused_prepare(const FusedLaunch& L);   // sets function attributes once
 cudaError_t fused_launch(const FusedLaunch& L, const void* in, void* out, cudaStream_t stream);
 int fused_max_active_clusters(const FusedLaunch& L);
+int fused_values_per_thread(bool dbl);
+
+// Adjoint launchers (adjoint.cu): same launch shape as the forward, no input staging.
+cudaError_t adjoint_prepare(const FusedLaunch& L);
+cudaError_t adjoint_launch(const FusedLaunch& L, const void* g, void* xb, cudaStream_t stream);
+size_t adjoint_smem_bytes(const FusedLaunch& L);
 
 }  // namespace adfft
 

@@ -11,8 +11,6 @@
 
 namespace adfft {
 
-int fused_values_per_thread(bool dbl);
-
 namespace {
 
 thread_local int g_last_error = ADFFT_OK;
@@ -191,6 +189,7 @@ int setup_fold(Plan& p) {
   L.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(p.batch, 65535));
   L.smem = smem;
   e = fused_prepare(L);
+  if (e == cudaSuccess) e = adjoint_prepare(L);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_status(e);
@@ -393,9 +392,18 @@ int adfft_execute(adfft_plan_t plan, const void* d_in, void* d_out, void* stream
 }
 
 int adfft_execute_adjoint(adfft_plan_t plan, const void* d_grad_out, void* d_grad_in, void* stream) {
-  (void)stream;
+  using namespace adfft;
   if (!plan || !d_grad_out || !d_grad_in) return ADFFT_ERR_INVALID_ARG;
-  return ADFFT_ERR_NOT_SUPPORTED;
+  Plan& p = plan->p;
+  if (!aligned16(d_grad_out) || !aligned16(d_grad_in)) return ADFFT_ERR_MISALIGNED;
+  if (overlaps(d_grad_out, p.out_bytes(), d_grad_in, p.in_bytes())) return ADFFT_ERR_OVERLAP;
+  if (p.batch == 0) return ADFFT_OK;
+  cudaError_t e = adjoint_launch(p.fused, d_grad_out, d_grad_in, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  return ADFFT_OK;
 }
 
 int adfft_execute_host(adfft_plan_t plan, const void* h_in, void* h_out, void* stream) {

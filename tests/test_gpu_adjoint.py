@@ -1,0 +1,141 @@
+"""GPU parity of the adjoint (backward) transform against the FP64 oracle, and
+the autograd binding against finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_16665_gb300 import adfft
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    adfft.load()
+    return torch
+
+
+def tol_for(M, dbl):
+    return 1e-12 if dbl else 2e-6 * max(1.0, np.log2(M))
+
+
+SIZES = [(1, 1), (2, 8), (4, 12), (8, 8), (16, 64), (64, 160), (64, 240), (128, 64), (128, 48),
+         (256, 2048), (1024, 4096), (2048, 5120), (4096, 15360), (8192, 65536), (16384, 131072)]
+
+
+@pytest.mark.parametrize("dtype_code", [adfft.R32, adfft.C64, adfft.R64, adfft.C128])
+@pytest.mark.parametrize("N,M", SIZES)
+def test_adjoint_matches_oracle(dtype_code, N, M):
+    torch = _torch()
+    dbl = dtype_code in (adfft.R64, adfft.C128)
+    real = dtype_code in (adfft.R32, adfft.R64)
+    if dtype_code == adfft.C128 and N >= 16384:
+        pytest.skip("complex128 sub-FFTs of 16384 points exceed one CTA's shared memory")
+    B = 2
+    rng = np.random.default_rng(N + 3 * M)
+    g = rng.standard_normal((B, M)) + 1j * rng.standard_normal((B, M))
+    g = g.astype(np.complex128 if dbl else np.complex64)
+    dev = torch.device("cuda:0")
+    gt = torch.from_numpy(g).to(dev)
+    plan = adfft.Plan(N, batch=B, dtype=dtype_code, M=M)
+    in_t = {adfft.R32: torch.float32, adfft.R64: torch.float64,
+            adfft.C64: torch.complex64, adfft.C128: torch.complex128}[dtype_code]
+    xb = torch.empty((B, N), dtype=in_t, device=dev)
+    plan.execute_adjoint(gt.data_ptr(), xb.data_ptr())
+    torch.cuda.synchronize()
+    got = xb.cpu().numpy()
+    if M * N > 3e8:
+        ref = oracle.alpha_dft_adjoint(g[:1].astype(np.complex128), N, real_input=real)
+        got = got[:1]
+    else:
+        ref = oracle.alpha_dft_adjoint(g.astype(np.complex128), N, real_input=real)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= tol_for(M, dbl), (err.max(), plan.info.fft_len, plan.info.residues)
+
+
+@pytest.mark.parametrize("dtype_code,N,M", [(adfft.C128, 64, 256), (adfft.R64, 64, 160),
+                                            (adfft.C64, 1024, 8192), (adfft.R32, 4096, 32768)])
+def test_dot_product_identity(dtype_code, N, M):
+    """<A x, g> = <x, A^H g> (real part for real x) through the two C-ABI calls."""
+    torch = _torch()
+    dbl = dtype_code in (adfft.R64, adfft.C128)
+    real = dtype_code in (adfft.R32, adfft.R64)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((1, N)) if real else rng.standard_normal((1, N)) + 1j * rng.standard_normal((1, N))
+    g = rng.standard_normal((1, M)) + 1j * rng.standard_normal((1, M))
+    in_np = {adfft.R32: np.float32, adfft.R64: np.float64, adfft.C64: np.complex64,
+             adfft.C128: np.complex128}[dtype_code]
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(x.astype(in_np)).to(dev)
+    gt = torch.from_numpy(g.astype(np.complex128 if dbl else np.complex64)).to(dev)
+    plan = adfft.Plan(N, batch=1, dtype=dtype_code, M=M)
+    X = torch.empty((1, M), dtype=torch.complex128 if dbl else torch.complex64, device=dev)
+    xb = torch.empty_like(xt)
+    plan.execute(xt.data_ptr(), X.data_ptr())
+    plan.execute_adjoint(gt.data_ptr(), xb.data_ptr())
+    torch.cuda.synchronize()
+    lhs = np.vdot(gt.cpu().numpy().astype(np.complex128), X.cpu().numpy().astype(np.complex128))
+    rhs = np.vdot(xb.cpu().numpy().astype(np.complex128), xt.cpu().numpy().astype(np.complex128))
+    if real:
+        lhs, rhs = lhs.real, rhs.real
+    tol = 1e-12 if dbl else 1e-5
+    assert abs(lhs - rhs) <= tol * max(1.0, abs(lhs))
+
+
+def test_inverse_of_eq7_round_trip():
+    """Second line of Eq. 7: with S = 1/(alpha N) the adjoint of the S = 1 forward
+    recovers x (alpha >= 1)."""
+    torch = _torch()
+    N, M = 2048, 2048 * 4
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((3, N)) + 1j * rng.standard_normal((3, N))
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(x).to(dev)
+    fwd = adfft.Plan(N, batch=3, dtype=adfft.C128, M=M)
+    fwd.set_scale(1.0)
+    inv = adfft.Plan(N, batch=3, dtype=adfft.C128, M=M)
+    inv.set_scale(1.0 / M)
+    X = torch.empty((3, M), dtype=torch.complex128, device=dev)
+    back = torch.empty_like(xt)
+    fwd.execute(xt.data_ptr(), X.data_ptr())
+    inv.execute_adjoint(X.data_ptr(), back.data_ptr())
+    torch.cuda.synchronize()
+    assert np.max(np.abs(back.cpu().numpy() - x)) < 1e-12
+
+
+def test_autograd_gradcheck_complex128():
+    torch = _torch()
+    from paper_2403_16665_gb300.autograd import AlphaDFT
+    x = torch.randn(2, 16, dtype=torch.complex128, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda t: AlphaDFT.apply(t, 40), (x,), eps=1e-6, atol=1e-8)
+
+
+def test_autograd_gradcheck_float64():
+    torch = _torch()
+    from paper_2403_16665_gb300.autograd import AlphaDFT
+    x = torch.randn(3, 32, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda t: AlphaDFT.apply(t, 128), (x,), eps=1e-6, atol=1e-8)
+
+
+def test_spectral_loss_gradient_against_oracle_adjoint():
+    """loss = sum |X - Y|^2 with random target spectra Y: the gradient is
+    2 Re(S A^H (X - Y)), checked against the FP64 oracle's adjoint."""
+    torch = _torch()
+    from paper_2403_16665_gb300.autograd import alpha_dft_autograd
+    rng = np.random.default_rng(11)
+    N, alpha = 4096, 2.5
+    M = int(alpha * N)
+    x_np = rng.standard_normal((4, N)).astype(np.float32)
+    Y_np = (rng.standard_normal((4, M)) + 1j * rng.standard_normal((4, M))).astype(np.complex64) * 1e-2
+    x = torch.from_numpy(x_np).cuda().requires_grad_(True)
+    Y = torch.from_numpy(Y_np).cuda()
+    X = alpha_dft_autograd(x, M=M)
+    loss = (X - Y).abs().pow(2).sum()
+    loss.backward()
+    X64 = oracle.alpha_dft(x_np.astype(np.float64), M)
+    ref = oracle.alpha_dft_adjoint(2 * (X64 - Y_np), N, real_input=True)
+    got = x.grad.cpu().numpy()
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 2e-6 * np.log2(M), err
