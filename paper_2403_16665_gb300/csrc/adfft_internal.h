@@ -9,6 +9,7 @@
 #include "adfft.h"
 #include "fft_device.cuh"
 #include "fused.cuh"
+#include "bluestein.cuh"
 
 namespace adfft {
 
@@ -18,6 +19,16 @@ struct FusedLaunch {
   int mode;        // LoadMode
   int r0;          // radix of the first pass
   bool dbl;        // double2 (true) or float2 elements
+  int threads;
+  int grid_y;
+  size_t smem;
+};
+
+// Launch geometry of the chirp-z kernel.
+struct BluesteinLaunch {
+  BluesteinArgs args;
+  int r0;
+  bool dbl;
   int threads;
   int grid_y;
   size_t smem;
@@ -38,6 +49,13 @@ struct Plan {
   FusedLaunch fused{};
   void* d_tw = nullptr;               // twiddle table of the fused path
   int* d_status = nullptr;            // device status word (0, or ADFFT_ERR_TIMEOUT)
+
+  // chirp-z path
+  bool blu_ok = false;
+  BluesteinLaunch blu{};
+  void* d_blu_tw = nullptr;           // W_L table
+  void* d_chirp = nullptr;            // chirp c_j
+  void* d_H = nullptr;                // per-chunk kernel spectra
 
   // host-memory staging of adfft_execute_host
   void* d_stage_in = nullptr;
@@ -60,6 +78,10 @@ int fused_values_per_thread(bool dbl);
 cudaError_t adjoint_prepare(const FusedLaunch& L);
 cudaError_t adjoint_launch(const FusedLaunch& L, const void* g, void* xb, cudaStream_t stream);
 size_t adjoint_smem_bytes(const FusedLaunch& L);
+
+// Chirp-z launchers (bluestein.cu).
+cudaError_t bluestein_prepare(const BluesteinLaunch& L);
+cudaError_t bluestein_launch(const BluesteinLaunch& L, const void* in, void* out, cudaStream_t stream);
 
 }  // namespace adfft
 

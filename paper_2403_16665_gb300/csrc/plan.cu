@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <new>
 #include <vector>
 
@@ -199,7 +200,155 @@ int setup_fold(Plan& p) {
   return ADFFT_OK;
 }
 
+// In-place iterative radix-2 FFT in double precision (host), forward sign.
+void host_fft(std::vector<std::complex<double>>& a) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    for (size_t i = 0; i < n; i += len) {
+      for (size_t k = 0; k < len / 2; ++k) {
+        double c, s;
+        root_of_unity((int64_t)k, (int64_t)len, &c, &s);
+        const std::complex<double> w(c, s);
+        const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+    }
+  }
+}
+
+// chirp c_j = exp(-pi i (j^2 mod 2M) / M), exact integer reduction of j^2
+std::complex<double> chirp(int64_t j, int64_t M) {
+  if (j < 0) j = -j;
+  const int64_t twoM = 2 * M;
+  const int64_t jj = (int64_t)(((__int128)j * j) % twoM);
+  double c, s;
+  root_of_unity(jj, twoM, &c, &s);
+  return {c, s};
+}
+
+template <typename T>
+int upload(void** dst, const std::vector<T>& v) {
+  const size_t bytes = v.size() * sizeof(T);
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *dst = nullptr;
+    return cuda_status(e);
+  }
+  e = cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice);
+  return cuda_status(e);
+}
+
+template <typename T>
+std::vector<T> flatten(const std::vector<std::complex<double>>& v) {
+  std::vector<T> o(2 * v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    o[2 * i] = (T)v[i].real();
+    o[2 * i + 1] = (T)v[i].imag();
+  }
+  return o;
+}
+
+// Configure the chirp-z path (any N, M); returns ADFFT_OK or why it does not apply.
+int setup_bluestein(Plan& p) {
+  const int64_t Lmax = p.dbl ? 8192 : 16384;
+  if (p.N > Lmax) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  int64_t L = 1;
+  while (L < p.N + p.M - 1 && L < Lmax) L <<= 1;
+  while (L < p.N) L <<= 1;
+  const int64_t B = L - p.N + 1;
+  const int64_t chunks = (p.M + B - 1) / B;
+  if (chunks > 65535 || p.M >= (int64_t(1) << 31)) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  const int vpt = fused_values_per_thread(p.dbl);
+  const size_t esz = p.dbl ? 16 : 8;
+  const int bits = (ilog2(L) + 1) / 2;
+  const int tw_n = (1 << bits) + (int)((L + (1 << bits) - 1) >> bits);
+  const int64_t region = L + L / 16 + 2;
+  const FusedSmem lay = fused_smem_layout(tw_n, 0, 1, (int)region, (int)esz);
+  if ((size_t)lay.total > kSmemLimit) return ADFFT_ERR_UNSUPPORTED_SIZE;
+
+  // host tables: W_L, chirp, per-chunk FFT_L(hs)/L
+  int lo_n, hi_n;
+  std::vector<std::complex<double>> ch((size_t)std::max(p.N, p.M));
+  for (size_t j = 0; j < ch.size(); ++j) ch[j] = chirp((int64_t)j, p.M);
+  std::vector<std::complex<double>> H((size_t)(chunks * L));
+  std::vector<std::complex<double>> seg((size_t)L);
+  for (int64_t c = 0; c < chunks; ++c) {
+    const int64_t m0 = c * B;
+    std::fill(seg.begin(), seg.end(), std::complex<double>(0, 0));
+    for (int64_t i = 0; i < p.N + B - 1 && i < L; ++i) seg[(size_t)i] = std::conj(chirp(m0 - (p.N - 1) + i, p.M));
+    host_fft(seg);
+    for (int64_t k = 0; k < L; ++k) H[(size_t)(c * L + k)] = seg[(size_t)k] / (double)L;
+  }
+  int rc;
+  if (p.dbl) {
+    auto tw = build_two_level<double>(L, bits, &lo_n, &hi_n);
+    if ((rc = upload(&p.d_blu_tw, tw)) != ADFFT_OK) return rc;
+    if ((rc = upload(&p.d_chirp, flatten<double>(ch))) != ADFFT_OK) return rc;
+    if ((rc = upload(&p.d_H, flatten<double>(H))) != ADFFT_OK) return rc;
+  } else {
+    auto tw = build_two_level<float>(L, bits, &lo_n, &hi_n);
+    if ((rc = upload(&p.d_blu_tw, tw)) != ADFFT_OK) return rc;
+    if ((rc = upload(&p.d_chirp, flatten<float>(ch))) != ADFFT_OK) return rc;
+    if ((rc = upload(&p.d_H, flatten<float>(H))) != ADFFT_OK) return rc;
+  }
+  BluesteinLaunch& BL = p.blu;
+  BluesteinArgs& b = BL.args;
+  memset(&b, 0, sizeof(b));
+  FusedArgs& a = b.f;
+  a.batch = p.batch;
+  a.M = p.M;
+  a.Np = (int)L;
+  a.logNp = ilog2(L);
+  a.P = 1;
+  a.q = 1;
+  a.RPC = 1;
+  a.C = 1;
+  a.Nc = (int)L;
+  a.Mc = (int)L;
+  a.Mt = (int)L;
+  a.tw_bits = bits;
+  a.tw_lo_n = lo_n;
+  a.tw_hi_n = hi_n;
+  a.tw = p.d_blu_tw;
+  a.scale = p.scale;
+  a.region = (int)region;
+  const int L2 = a.logNp;
+  const int lr0 = (L2 == 0) ? 0 : (L2 % 4 ? L2 % 4 : 4);
+  a.nrad = 1 + (L2 - lr0) / 4;
+  a.status = p.d_status;
+  b.chirp = p.d_chirp;
+  b.H = p.d_H;
+  b.N = p.N;
+  b.B = (int)B;
+  b.chunks = (int)chunks;
+  b.real_in = p.real ? 1 : 0;
+  BL.r0 = 1 << lr0;
+  BL.dbl = p.dbl;
+  BL.threads = std::max(32, (int)((L / vpt + 31) / 32 * 32));
+  BL.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(p.batch, 65535));
+  BL.smem = (size_t)lay.total;
+  cudaError_t e = bluestein_prepare(BL);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  p.blu_ok = true;
+  return ADFFT_OK;
+}
+
 void release(Plan& p) {
+  for (void** q : {&p.d_blu_tw, &p.d_chirp, &p.d_H}) {
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+  }
   if (p.d_status) cudaFree(p.d_status);
   p.d_status = nullptr;
   if (p.d_tw) cudaFree(p.d_tw);
@@ -278,12 +427,13 @@ adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dty
       return fail(cuda_status(e), h);
     }
   }
-  int rc = setup_fold(p);
-  if (rc == ADFFT_OK) {
-    p.algo = ADFFT_ALGO_FOLD;
-  } else {
-    return fail(rc, h);
-  }
+  const int rc_fold = setup_fold(p);
+  if (rc_fold != ADFFT_OK && rc_fold != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_fold, h);
+  const int rc_blu = setup_bluestein(p);
+  if (rc_blu != ADFFT_OK && rc_blu != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_blu, h);
+  if (p.fold_ok) p.algo = ADFFT_ALGO_FOLD;
+  else if (p.blu_ok) p.algo = ADFFT_ALGO_BLUESTEIN;
+  else return fail(ADFFT_ERR_UNSUPPORTED_SIZE, h);
   g_last_error = ADFFT_OK;
   return h;
 }
@@ -329,17 +479,27 @@ int adfft_plan_set_scale(adfft_plan_t plan, double S) {
   if (!plan || !isfinite(S)) return ADFFT_ERR_INVALID_ARG;
   plan->p.scale = S;
   plan->p.fused.args.scale = S;
+  plan->p.blu.args.f.scale = S;
   return ADFFT_OK;
 }
 
 int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
   if (!plan) return ADFFT_ERR_INVALID_ARG;
-  if (algo == ADFFT_ALGO_AUTO || algo == ADFFT_ALGO_FOLD) {
-    if (!plan->p.fold_ok) return ADFFT_ERR_NOT_SUPPORTED;
-    plan->p.algo = ADFFT_ALGO_FOLD;
+  Plan& p = plan->p;
+  if (algo == ADFFT_ALGO_AUTO) {
+    p.algo = p.fold_ok ? ADFFT_ALGO_FOLD : ADFFT_ALGO_BLUESTEIN;
     return ADFFT_OK;
   }
-  if (algo == ADFFT_ALGO_BLUESTEIN) return ADFFT_ERR_NOT_SUPPORTED;
+  if (algo == ADFFT_ALGO_FOLD) {
+    if (!p.fold_ok) return ADFFT_ERR_NOT_SUPPORTED;
+    p.algo = algo;
+    return ADFFT_OK;
+  }
+  if (algo == ADFFT_ALGO_BLUESTEIN) {
+    if (!p.blu_ok) return ADFFT_ERR_NOT_SUPPORTED;
+    p.algo = algo;
+    return ADFFT_OK;
+  }
   return ADFFT_ERR_INVALID_ARG;
 }
 
@@ -362,10 +522,17 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
   info->batch = p.batch;
   info->dtype = p.dtype;
   info->algo = p.algo;
-  info->fft_len = p.fused.args.Np;
-  info->residues = p.fused.args.P;
-  info->fold = p.fused.args.q;
-  info->cluster = p.fused.args.C;
+  if (p.algo == ADFFT_ALGO_BLUESTEIN) {
+    info->fft_len = p.blu.args.f.Np;
+    info->residues = p.blu.args.chunks;
+    info->fold = 0;
+    info->cluster = 1;
+  } else {
+    info->fft_len = p.fused.args.Np;
+    info->residues = p.fused.args.P;
+    info->fold = p.fused.args.q;
+    info->cluster = p.fused.args.C;
+  }
   info->passes = 1;
   info->scale = p.scale;
   return ADFFT_OK;
@@ -383,7 +550,9 @@ int adfft_execute(adfft_plan_t plan, const void* d_in, void* d_out, void* stream
   if (!aligned16(d_in) || !aligned16(d_out)) return ADFFT_ERR_MISALIGNED;
   if (overlaps(d_in, p.in_bytes(), d_out, p.out_bytes())) return ADFFT_ERR_OVERLAP;
   if (p.batch == 0) return ADFFT_OK;
-  cudaError_t e = fused_launch(p.fused, d_in, d_out, (cudaStream_t)stream);
+  cudaError_t e = (p.algo == ADFFT_ALGO_BLUESTEIN)
+                      ? bluestein_launch(p.blu, d_in, d_out, (cudaStream_t)stream)
+                      : fused_launch(p.fused, d_in, d_out, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_status(e);
@@ -398,6 +567,7 @@ int adfft_execute_adjoint(adfft_plan_t plan, const void* d_grad_out, void* d_gra
   if (!aligned16(d_grad_out) || !aligned16(d_grad_in)) return ADFFT_ERR_MISALIGNED;
   if (overlaps(d_grad_out, p.out_bytes(), d_grad_in, p.in_bytes())) return ADFFT_ERR_OVERLAP;
   if (p.batch == 0) return ADFFT_OK;
+  if (!p.fold_ok) return ADFFT_ERR_NOT_SUPPORTED;   // the adjoint kernel uses the fold decomposition
   cudaError_t e = adjoint_launch(p.fused, d_grad_out, d_grad_in, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -1,0 +1,103 @@
+"""GPU parity of the chirp-z (Bluestein) path against the FP64 oracle: sizes the
+fold path cannot take (gcd(M, N) not a power of two), and the complex64
+N = 8192, alpha in {2.5, 3.75} workload forced onto the chirp-z kernel."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_16665_gb300 import adfft, signals
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    adfft.load()
+    return torch
+
+
+def tol_for(M, dbl):
+    return 1e-12 if dbl else 2e-6 * max(1.0, np.log2(M))
+
+
+def run(torch, x, M, dtype_code, algo=None):
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    B, N = xt.shape
+    plan = adfft.Plan(N, batch=B, dtype=dtype_code, M=M)
+    if algo is not None:
+        plan.set_algorithm(algo)
+    dbl = dtype_code in (adfft.R64, adfft.C128)
+    X = torch.empty((B, M), dtype=torch.complex128 if dbl else torch.complex64, device=dev)
+    plan.execute(xt.data_ptr(), X.data_ptr())
+    torch.cuda.synchronize()
+    return X.cpu().numpy(), plan
+
+
+NP = {adfft.R32: np.float32, adfft.R64: np.float64, adfft.C64: np.complex64, adfft.C128: np.complex128}
+
+
+@pytest.mark.parametrize("dtype_code", [adfft.R32, adfft.C64, adfft.R64, adfft.C128])
+@pytest.mark.parametrize("N,M", [(7, 7), (9, 6), (3, 10), (100, 250), (1000, 2000), (1000, 2500),
+                                 (1000, 300), (999, 3996), (3000, 7500), (5000, 12345)])
+def test_chirp_z_sizes(dtype_code, N, M):
+    torch = _torch()
+    dbl = dtype_code in (adfft.R64, adfft.C128)
+    if dbl and N > 8192:
+        pytest.skip("beyond the fp64 chirp-z length")
+    rng = np.random.default_rng(N * 13 + M)
+    x = rng.standard_normal((2, N))
+    if dtype_code in (adfft.C64, adfft.C128):
+        x = x + 1j * rng.standard_normal((2, N))
+    x = x.astype(NP[dtype_code])
+    got, plan = run(torch, x, M, dtype_code, algo=adfft.ALGO_BLUESTEIN)
+    assert plan.info.algo == adfft.ALGO_BLUESTEIN
+    ref = oracle.alpha_dft(x.astype(np.complex128), M)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= tol_for(M, dbl), (err.max(), plan.info.fft_len, plan.info.residues)
+
+
+@pytest.mark.parametrize("alpha", [2.5, 3.75])
+def test_complex_workload_forced_chirp_z(alpha):
+    """1024-signal complex64 workload shape (8 signals here), N = 8192, on the
+    chirp-z kernel; sampled bins against the oracle and all bins against the fold path."""
+    torch = _torch()
+    x, _ = signals.batch_c64(batch=8, alpha=alpha)
+    M = int(round(alpha * 8192))
+    got, plan = run(torch, x, M, adfft.C64, algo=adfft.ALGO_BLUESTEIN)
+    assert plan.info.algo == adfft.ALGO_BLUESTEIN
+    rng = np.random.default_rng(5)
+    bins = np.unique(np.concatenate([np.arange(16), M - 1 - np.arange(16), rng.integers(0, M, 2000)]))
+    ref = oracle.alpha_dft(x.astype(np.complex128), M, bins=bins)
+    err = np.linalg.norm(got[:, bins] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= tol_for(M, False)
+    fold, _ = run(torch, x, M, adfft.C64, algo=adfft.ALGO_FOLD)
+    d = np.linalg.norm(got - fold, axis=1) / np.linalg.norm(fold, axis=1)
+    assert d.max() <= 2 * tol_for(M, False)
+
+
+@pytest.mark.parametrize("N,M", [(1000, 2000), (1000, 2500), (999, 3996), (100, 250)])
+def test_auto_picks_chirp_z_when_gcd_is_not_a_power_of_two(N, M):
+    _torch()
+    for code in (adfft.R32, adfft.C64):
+        assert adfft.Plan(N, batch=1, dtype=code, M=M).info.algo == adfft.ALGO_BLUESTEIN
+
+
+def test_single_real_fp64_chirp_z():
+    torch = _torch()
+    x, _ = signals.single_r64()
+    got, _ = run(torch, x, 4096, adfft.R64, algo=adfft.ALGO_BLUESTEIN)
+    ref = oracle.alpha_dft(x, 4096)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-12
+
+
+def test_adjoint_unavailable_without_fold():
+    torch = _torch()
+    plan = adfft.Plan(1000, batch=1, dtype=adfft.C64, M=2500)
+    g = torch.zeros((1, 2500), dtype=torch.complex64, device="cuda")
+    xb = torch.zeros((1, 1000), dtype=torch.complex64, device="cuda")
+    with pytest.raises(adfft.AdfftError) as e:
+        plan.execute_adjoint(g.data_ptr(), xb.data_ptr())
+    assert e.value.code == -9
