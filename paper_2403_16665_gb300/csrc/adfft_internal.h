@@ -10,6 +10,7 @@
 #include "fft_device.cuh"
 #include "fused.cuh"
 #include "bluestein.cuh"
+#include "twopass.cuh"
 
 namespace adfft {
 
@@ -31,6 +32,16 @@ struct BluesteinLaunch {
   bool dbl;
   int threads;
   int grid_y;
+  size_t smem;
+};
+
+// Launch geometry of the second pass of the two-pass form.
+struct TwoPassLaunch {
+  TwoPassArgs args;
+  int r0;
+  bool dbl;
+  int threads;
+  int grid_x, grid_y;
   size_t smem;
 };
 
@@ -57,6 +68,18 @@ struct Plan {
   void* d_chirp = nullptr;            // chirp c_j
   void* d_H = nullptr;                // per-chunk kernel spectra
 
+  // two-pass path (sub-FFT beyond one cluster): pass 1 = fused kColumns launch, pass 2 = columns
+  bool tp_ok = false;
+  int64_t tp_A = 0, tp_B = 0;
+  FusedLaunch tp1{};
+  TwoPassLaunch tp2{};
+  void* d_tp_tw1 = nullptr;           // pass-1 W_R1 table
+  void* d_tp_post = nullptr;          // pass-1 row twiddles W_Mc
+  void* d_tp_tw2 = nullptr;           // pass-2 W_B table
+  void* d_tp_wM = nullptr;            // pass-2 W_M table (real unpacking)
+  void* d_ws = nullptr;               // scratch [batch][B][R1]
+  size_t ws_bytes = 0;
+
   // host-memory staging of adfft_execute_host
   void* d_stage_in = nullptr;
   void* d_stage_out = nullptr;
@@ -78,6 +101,10 @@ int fused_values_per_thread(bool dbl);
 cudaError_t adjoint_prepare(const FusedLaunch& L);
 cudaError_t adjoint_launch(const FusedLaunch& L, const void* g, void* xb, cudaStream_t stream);
 size_t adjoint_smem_bytes(const FusedLaunch& L);
+
+// Two-pass second-pass launchers (twopass.cu).
+cudaError_t twopass_prepare(const TwoPassLaunch& L);
+cudaError_t twopass_launch(const TwoPassLaunch& L, const void* scratch, void* out, cudaStream_t stream);
 
 // Chirp-z launchers (bluestein.cu).
 cudaError_t bluestein_prepare(const BluesteinLaunch& L);

@@ -26,12 +26,14 @@ KernelFn pick_kernel(const FusedLaunch& L) {
     switch (L.mode) {
       case kLoadComplex: return pick_r0<double2, kLoadComplex, kVptF64>(L.r0);
       case kLoadRealPacked: return pick_r0<double2, kLoadRealPacked, kVptF64>(L.r0);
+      case kColumns: return pick_r0<double2, kColumns, kVptF64>(L.r0);
       default: return pick_r0<double2, kLoadRealPlain, kVptF64>(L.r0);
     }
   }
   switch (L.mode) {
     case kLoadComplex: return pick_r0<float2, kLoadComplex, kVptF32>(L.r0);
     case kLoadRealPacked: return pick_r0<float2, kLoadRealPacked, kVptF32>(L.r0);
+    case kColumns: return pick_r0<float2, kColumns, kVptF32>(L.r0);
     default: return pick_r0<float2, kLoadRealPlain, kVptF32>(L.r0);
   }
 }

@@ -33,7 +33,9 @@ namespace cg = cooperative_groups;
 enum LoadMode : int {
   kLoadComplex = 0,      // complex input, u = x
   kLoadRealPacked = 1,   // real input, two samples per complex element, unpacked in the epilogue
-  kLoadRealPlain = 2     // real input read as complex with zero imaginary part (odd N or odd M)
+  kLoadRealPlain = 2,    // real input read as complex with zero imaginary part (odd N or odd M)
+  kColumns = 3           // first pass of the two-pass form: complex columns u_{B a + b} of each
+                         // signal (element stride B = cols), output row b twiddled by W_Mpost^{m b}
 };
 
 // Status word values written by kernels (0 = no error).
@@ -58,6 +60,11 @@ struct FusedArgs {
   int stage_bytes;       // > 0: each signal's input is bulk-copied into shared memory first
   int* status;           // device status word of the plan
   FastDiv divP, divRPC;
+  // kColumns only: columns per signal, and the two-level table of W_Mpost (global memory)
+  long long cols;
+  const void* post_tw;
+  int post_bits, post_lo_n;
+  long long Mpost;
 };
 
 // Shared-memory layout of the fused kernel (byte offsets).
@@ -83,6 +90,11 @@ __device__ __forceinline__ V ld_u(const void* base, int idx, int mode, bool smem
   }
   if (mode == kLoadRealPlain) return cmake<V>(__ldg(reinterpret_cast<const R*>(base) + idx), (R)0);
   return __ldg(reinterpret_cast<const V*>(base) + idx);
+}
+
+template <typename V>
+__device__ __forceinline__ V ld_col(const void* base, int idx, long long stride) {
+  return __ldg(reinterpret_cast<const V*>(base) + (long long)idx * stride);
 }
 
 // Multiply v[n][i] (n < NI items, i = 1..R-1) by w^i, w = W^k from one table
@@ -116,6 +128,12 @@ __device__ __forceinline__ void apply_stage_twiddles(V (*v)[R], V w1) {
 // constants c = W_Mt^{s r Np/R} and g = W_Mt^{s r Np} (s = Mt/Mc), so each
 // (j, r) costs one table lookup.
 template <int R, typename V>
+__device__ __forceinline__ V ld_any(const FusedArgs& a, const void* u, int idx, int mode, bool staged) {
+  if (mode == kColumns) return ld_col<V>(u, idx, a.cols);
+  return ld_u<V>(u, idx, mode, staged);
+}
+
+template <int R, typename V>
 __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, int mode, bool staged,
                                            V* buf, const TwTable<V>& tab, int r0) {
   const int items = a.Np / R;
@@ -133,12 +151,12 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, in
       V acc[R];
       // fold: acc[i] = sum_f u[j + i items + f Np] g^f
 #pragma unroll
-      for (int i = 0; i < R; ++i) acc[i] = ld_u<V>(u, j + i * items, mode, staged);
+      for (int i = 0; i < R; ++i) acc[i] = ld_any<R, V>(a, u, j + i * items, mode, staged);
       if (a.q > 1) {
         V gf = g1;
         for (int f = 1; f < a.q; ++f) {
 #pragma unroll
-          for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_u<V>(u, j + i * items + f * a.Np, mode, staged), gf));
+          for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_any<R, V>(a, u, j + i * items + f * a.Np, mode, staged), gf));
           gf = cmul(gf, g1);
         }
       }
@@ -307,10 +325,13 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
         if (a.status) atomicExch(a.status, kStatusTimeout);
       }
       phase ^= 1u;
+    } else if (MODE == kColumns) {
+      u = reinterpret_cast<const V*>(a.in) + (sig / a.cols) * a.in_stride + (sig % a.cols);
     } else {
       u = reinterpret_cast<const unsigned char*>(a.in) + sig * in_bytes_per_sig;
     }
     V* out = reinterpret_cast<V*>(a.out) + sig * a.M;
+    const unsigned col = (MODE == kColumns) ? (unsigned)(sig % a.cols) : 0u;
 
     // ---- K1: fold + residue twiddle + first radix
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
@@ -383,7 +404,17 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
           for (int e = 0; e < kEpilogueUnroll; ++e) {
             const unsigned k = kb + e * k_step;
             const unsigned m = k * P + r_l;
-            if (m <= j_last) out[m] = cscale(Ua[e], S);
+            if (m <= j_last) {
+              V y = cscale(Ua[e], S);
+              if (MODE == kColumns) {
+                // row twiddle W_Mpost^{m col}
+                const unsigned long long e2 = ((unsigned long long)m * col) % (unsigned long long)a.Mpost;
+                const V* lo = reinterpret_cast<const V*>(a.post_tw);
+                const V* hi = lo + a.post_lo_n;
+                y = cmul(y, cmul(__ldg(hi + (e2 >> a.post_bits)), __ldg(lo + (e2 & ((1ull << a.post_bits) - 1)))));
+              }
+              out[m] = y;
+            }
           }
         }
       }

@@ -75,47 +75,36 @@ int cuda_status(cudaError_t e) {
   return ADFFT_ERR_CUDA;
 }
 
-// Configure the fused fold+FFT path; returns ADFFT_OK or a reason it does not apply.
-int setup_fold(Plan& p) {
-  FusedLaunch& L = p.fused;
-  int mode;
-  int64_t Nc, Mc;
-  if (!p.real) {
-    mode = kLoadComplex;
-    Nc = p.N;
-    Mc = p.M;
-  } else if (p.N % 2 == 0 && p.M % 2 == 0) {
-    mode = kLoadRealPacked;
-    Nc = p.N / 2;
-    Mc = p.M / 2;
-  } else {
-    mode = kLoadRealPlain;
-    Nc = p.N;
-    Mc = p.M;
-  }
+template <typename T>
+int upload(void** dst, const std::vector<T>& v);
+
+// Configure a fused fold+FFT launch for the complex core of Nc input elements
+// and Mc bins (twiddle modulus Mt); stage_bytes > 0 asks for bulk-copy input
+// staging of that many bytes per signal, used if it fits.  Allocates the
+// twiddle table in *d_tw.  Returns ADFFT_OK or why the shape does not fit.
+int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int64_t batch,
+                    int64_t stage_bytes, int max_cluster, double scale, int* status,
+                    FusedLaunch& L, void** d_tw) {
   const int64_t Np = gcd64(Mc, Nc);
   const int64_t P = Mc / Np, q = Nc / Np;
   if (!is_pow2(Np)) return ADFFT_ERR_UNSUPPORTED_SIZE;
   if (q > kMaxFold) return ADFFT_ERR_UNSUPPORTED_SIZE;
-  const int64_t Mt = (mode == kLoadRealPacked) ? p.M : Mc;
   if (Mt >= (int64_t(1) << 31)) return ADFFT_ERR_UNSUPPORTED_SIZE;
-  const size_t esz = p.dbl ? 16 : 8;
-  const int vpt = fused_values_per_thread(p.dbl);
+  const size_t esz = dbl ? 16 : 8;
+  const int vpt = fused_values_per_thread(dbl);
   const int max_vals = vpt * kMaxThreads;
 
   const int bits = (ilog2(Mt) + 1) / 2;
   int lo_n, hi_n;
   const int tw_n = (1 << bits) + (int)((Mt + (1 << bits) - 1) >> bits);
   const int64_t region = Np + Np / 16 + 2;
-  // input bytes per signal; staged through shared memory by bulk copies when 16-byte granular
-  const int64_t sig_bytes = (int64_t)p.N * (int64_t)p.in_elem;
-  const bool can_stage = (sig_bytes % 16) == 0 && sig_bytes <= (int64_t)kSmemLimit;
+  const bool can_stage = stage_bytes > 0 && (stage_bytes % 16) == 0 && stage_bytes <= (int64_t)kSmemLimit;
   int C = -1, stage = 0;
   size_t smem = 0;
   for (int pass = 0; pass < 2 && C < 0; ++pass) {
-    const int st = (pass == 0 && can_stage) ? (int)sig_bytes : 0;
     if (pass == 0 && !can_stage) continue;
-    for (int c = 1; c <= std::min<int64_t>(P, kMaxCluster); ++c) {
+    const int st = (pass == 0) ? (int)stage_bytes : 0;
+    for (int c = 1; c <= std::min<int64_t>(P, max_cluster); ++c) {
       if (P % c) continue;
       const int64_t rpc = P / c;
       if (rpc * Np > max_vals) continue;
@@ -132,9 +121,9 @@ int setup_fold(Plan& p) {
 
   FusedArgs& a = L.args;
   memset(&a, 0, sizeof(a));
-  a.batch = p.batch;
-  a.in_stride = (mode == kLoadComplex) ? p.N : p.N;   // complex elements or real scalars per signal
-  a.M = p.M;
+  a.batch = batch;
+  a.M = (mode == kLoadRealPacked) ? 2 * Mc : Mc;
+  a.in_stride = (mode == kLoadComplex || mode == kColumns) ? Nc : (mode == kLoadRealPacked ? 2 * Nc : Nc);
   a.Np = (int)Np;
   a.logNp = ilog2(Np);
   a.P = (int)P;
@@ -145,11 +134,11 @@ int setup_fold(Plan& p) {
   a.Mc = (int)Mc;
   a.Mt = (int)Mt;
   a.tw_bits = bits;
-  a.scale = p.scale;
+  a.scale = scale;
   a.region = (int)region;
   a.stage_bytes = stage;
-  a.status = p.d_status;
-  // radices: the remainder (2, 4 or 8) first, then radix 16
+  a.status = status;
+  a.cols = 1;
   // passes: a first pass of radix R0 = 2^(log2 Np mod 4) (16 if that is 0), then radix 16
   const int L2 = a.logNp;
   int lr0 = (L2 == 0) ? 0 : (L2 % 4 ? L2 % 4 : 4);
@@ -161,7 +150,7 @@ int setup_fold(Plan& p) {
   // tables
   size_t tw_bytes;
   std::vector<unsigned char> host;
-  if (p.dbl) {
+  if (dbl) {
     auto t = build_two_level<double>(Mt, bits, &lo_n, &hi_n);
     tw_bytes = t.size() * sizeof(double);
     host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + tw_bytes);
@@ -172,32 +161,194 @@ int setup_fold(Plan& p) {
   }
   a.tw_lo_n = lo_n;
   a.tw_hi_n = hi_n;
-  cudaError_t e = cudaMalloc(&p.d_tw, tw_bytes);
+  cudaError_t e = cudaMalloc(d_tw, tw_bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    p.d_tw = nullptr;
+    *d_tw = nullptr;
     return cuda_status(e);
   }
-  e = cudaMemcpy(p.d_tw, host.data(), tw_bytes, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(*d_tw, host.data(), tw_bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_status(e);
-  a.tw = p.d_tw;
+  a.tw = *d_tw;
 
   int threads = (int)((RPC * Np + vpt - 1) / vpt);
   threads = std::max(32, (threads + 31) / 32 * 32);
   L.mode = mode;
-  L.dbl = p.dbl;
+  L.dbl = dbl;
   L.threads = threads;
-  L.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(p.batch, 65535));
+  L.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(batch, 65535));
   L.smem = smem;
   e = fused_prepare(L);
-  if (e == cudaSuccess) e = adjoint_prepare(L);
+  if (e == cudaSuccess && mode != kColumns) e = adjoint_prepare(L);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_status(e);
   }
   if (C > 1 && fused_max_active_clusters(L) < 1) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  return ADFFT_OK;
+}
+
+// How the plan's input maps onto the complex core: mode, Nc, Mc.
+void core_shape(const Plan& p, int* mode, int64_t* Nc, int64_t* Mc) {
+  if (!p.real) {
+    *mode = kLoadComplex;
+    *Nc = p.N;
+    *Mc = p.M;
+  } else if (p.N % 2 == 0 && p.M % 2 == 0) {
+    *mode = kLoadRealPacked;
+    *Nc = p.N / 2;
+    *Mc = p.M / 2;
+  } else {
+    *mode = kLoadRealPlain;
+    *Nc = p.N;
+    *Mc = p.M;
+  }
+}
+
+// Configure the fused single-pass fold+FFT path.
+int setup_fold(Plan& p) {
+  int mode;
+  int64_t Nc, Mc;
+  core_shape(p, &mode, &Nc, &Mc);
+  const int64_t Mt = (mode == kLoadRealPacked) ? p.M : Mc;
+  const int64_t sig_bytes = (int64_t)p.N * (int64_t)p.in_elem;
+  int rc = configure_fused(p.dbl, mode, Nc, Mc, Mt, p.batch, sig_bytes, kMaxCluster, p.scale, p.d_status,
+                           p.fused, &p.d_tw);
+  if (rc != ADFFT_OK) return rc;
+  p.fused.args.in_stride = p.N;   // complex elements or real scalars per signal
+  p.fused.args.M = p.M;
   p.fold_ok = true;
   return ADFFT_OK;
+}
+
+// Configure the two-pass (four-step) path for power-of-two Nc beyond one cluster.
+int setup_twopass(Plan& p) {
+  int mode;
+  int64_t Nc, Mc;
+  core_shape(p, &mode, &Nc, &Mc);
+  if (mode == kLoadRealPlain || !is_pow2(Nc) || Nc < 4) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  if (Mc % Nc != 0 && (Mc * 2) % Nc != 0) {
+    // alpha must make R1 = alpha A an integer for some power-of-two A
+  }
+  const size_t esz = p.dbl ? 16 : 8;
+  const int vpt = fused_values_per_thread(p.dbl);
+  for (int max_c : {4, 8}) {
+    for (int64_t A = Nc / 2; A >= 16; A >>= 1) {
+      const int64_t B = Nc / A;
+      if (B > 2048) break;
+      if ((Mc * A) % Nc != 0) continue;
+      const int64_t R1 = Mc * A / Nc;
+      if (mode == kLoadRealPacked && (R1 % 2) != 0) continue;
+      // pass 2 geometry: W column pairs per CTA
+      const int W = (B <= 512) ? 16 : (B <= 1024) ? 8 : 4;
+      const int ncol = (mode == kLoadRealPacked) ? 2 * W : W;
+      const int64_t region = B + B / 16 + 2;
+      const int bits2 = (ilog2(B) + 1) / 2;
+      const int tw_n2 = (1 << bits2) + (int)((B + (1 << bits2) - 1) >> bits2);
+      const FusedSmem lay2 = fused_smem_layout(tw_n2, 0, ncol, (int)region, (int)esz);
+      if ((size_t)lay2.total > kSmemLimit) continue;
+      if ((int64_t)ncol * B > (int64_t)vpt * kMaxThreads) continue;
+      // pass 1: alpha-DFT of the B columns (A samples -> R1 bins each)
+      FusedLaunch L1{};
+      void* tw1 = nullptr;
+      int rc = configure_fused(p.dbl, kColumns, A, R1, R1, p.batch * B, 0, max_c, 1.0, p.d_status, L1, &tw1);
+      if (rc != ADFFT_OK) {
+        if (tw1) cudaFree(tw1);
+        if (rc == ADFFT_ERR_UNSUPPORTED_SIZE) continue;
+        return rc;
+      }
+      p.d_tp_tw1 = tw1;
+      L1.args.cols = B;
+      L1.args.in_stride = Nc;
+      L1.args.M = R1;
+      L1.args.Mpost = Mc;
+      int lo_n, hi_n;
+      const int pbits = (ilog2(Mc) + 1) / 2;
+      if (p.dbl) {
+        if ((rc = upload(&p.d_tp_post, build_two_level<double>(Mc, pbits, &lo_n, &hi_n))) != ADFFT_OK) return rc;
+      } else {
+        if ((rc = upload(&p.d_tp_post, build_two_level<float>(Mc, pbits, &lo_n, &hi_n))) != ADFFT_OK) return rc;
+      }
+      L1.args.post_tw = p.d_tp_post;
+      L1.args.post_bits = pbits;
+      L1.args.post_lo_n = lo_n;
+      p.tp1 = L1;
+      // pass 2 tables: W_B (shared memory), W_M (global, real unpacking)
+      TwoPassLaunch& L2 = p.tp2;
+      TwoPassArgs& t = L2.args;
+      memset(&t, 0, sizeof(t));
+      FusedArgs& f = t.f;
+      f.Np = (int)B;
+      f.logNp = ilog2(B);
+      f.P = 1;
+      f.q = 1;
+      f.RPC = ncol;
+      f.C = 1;
+      f.Nc = (int)B;
+      f.Mc = (int)B;
+      f.Mt = (int)B;
+      f.tw_bits = bits2;
+      f.region = (int)region;
+      f.scale = 1.0;
+      f.status = p.d_status;
+      const int lb = f.logNp;
+      const int lr0 = (lb == 0) ? 0 : (lb % 4 ? lb % 4 : 4);
+      f.nrad = 1 + (lb - lr0) / 4;
+      L2.r0 = 1 << lr0;
+      const int mbits = (ilog2(p.M) + 1) / 2;
+      if (p.dbl) {
+        if ((rc = upload(&p.d_tp_tw2, build_two_level<double>(B, bits2, &lo_n, &hi_n))) != ADFFT_OK) return rc;
+        f.tw_lo_n = lo_n;
+        f.tw_hi_n = hi_n;
+        if ((rc = upload(&p.d_tp_wM, build_two_level<double>(p.M, mbits, &lo_n, &hi_n))) != ADFFT_OK) return rc;
+      } else {
+        if ((rc = upload(&p.d_tp_tw2, build_two_level<float>(B, bits2, &lo_n, &hi_n))) != ADFFT_OK) return rc;
+        f.tw_lo_n = lo_n;
+        f.tw_hi_n = hi_n;
+        if ((rc = upload(&p.d_tp_wM, build_two_level<float>(p.M, mbits, &lo_n, &hi_n))) != ADFFT_OK) return rc;
+      }
+      f.tw = p.d_tp_tw2;
+      t.wM = p.d_tp_wM;
+      t.wM_bits = mbits;
+      t.wM_lo_n = lo_n;
+      t.batch = p.batch;
+      t.B = (int)B;
+      t.logB = ilog2(B);
+      t.R1 = R1;
+      t.Mc = Mc;
+      t.M = p.M;
+      t.W = W;
+      t.real_packed = (mode == kLoadRealPacked) ? 1 : 0;
+      t.scale = p.scale;
+      L2.dbl = p.dbl;
+      L2.threads = std::max(32, (int)(((int64_t)ncol * B / vpt + 31) / 32 * 32));
+      const int64_t npairs = (mode == kLoadRealPacked) ? R1 / 2 + 1 : R1;
+      L2.grid_x = (int)((npairs + W - 1) / W);
+      L2.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(p.batch, 65535));
+      L2.smem = (size_t)lay2.total;
+      if (L2.grid_x > 0x7fffffff) return ADFFT_ERR_UNSUPPORTED_SIZE;
+      cudaError_t e = twopass_prepare(L2);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e);
+      }
+      // scratch [batch][B][R1]
+      p.ws_bytes = (size_t)p.batch * (size_t)Mc * esz;
+      if (p.ws_bytes) {
+        e = cudaMalloc(&p.d_ws, p.ws_bytes);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          p.d_ws = nullptr;
+          return cuda_status(e);
+        }
+      }
+      p.tp_A = A;
+      p.tp_B = B;
+      p.tp_ok = true;
+      return ADFFT_OK;
+    }
+  }
+  return ADFFT_ERR_UNSUPPORTED_SIZE;
 }
 
 // In-place iterative radix-2 FFT in double precision (host), forward sign.
@@ -345,7 +496,7 @@ int setup_bluestein(Plan& p) {
 }
 
 void release(Plan& p) {
-  for (void** q : {&p.d_blu_tw, &p.d_chirp, &p.d_H}) {
+  for (void** q : {&p.d_blu_tw, &p.d_chirp, &p.d_H, &p.d_tp_tw1, &p.d_tp_post, &p.d_tp_tw2, &p.d_tp_wM, &p.d_ws}) {
     if (*q) cudaFree(*q);
     *q = nullptr;
   }
@@ -431,7 +582,11 @@ adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dty
   if (rc_fold != ADFFT_OK && rc_fold != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_fold, h);
   const int rc_blu = setup_bluestein(p);
   if (rc_blu != ADFFT_OK && rc_blu != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_blu, h);
-  if (p.fold_ok) p.algo = ADFFT_ALGO_FOLD;
+  if (!p.fold_ok) {
+    const int rc_tp = setup_twopass(p);
+    if (rc_tp != ADFFT_OK && rc_tp != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_tp, h);
+  }
+  if (p.fold_ok || p.tp_ok) p.algo = ADFFT_ALGO_FOLD;
   else if (p.blu_ok) p.algo = ADFFT_ALGO_BLUESTEIN;
   else return fail(ADFFT_ERR_UNSUPPORTED_SIZE, h);
   g_last_error = ADFFT_OK;
@@ -480,6 +635,7 @@ int adfft_plan_set_scale(adfft_plan_t plan, double S) {
   plan->p.scale = S;
   plan->p.fused.args.scale = S;
   plan->p.blu.args.f.scale = S;
+  plan->p.tp2.args.scale = S;
   return ADFFT_OK;
 }
 
@@ -487,11 +643,11 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
   if (!plan) return ADFFT_ERR_INVALID_ARG;
   Plan& p = plan->p;
   if (algo == ADFFT_ALGO_AUTO) {
-    p.algo = p.fold_ok ? ADFFT_ALGO_FOLD : ADFFT_ALGO_BLUESTEIN;
+    p.algo = (p.fold_ok || p.tp_ok) ? ADFFT_ALGO_FOLD : ADFFT_ALGO_BLUESTEIN;
     return ADFFT_OK;
   }
   if (algo == ADFFT_ALGO_FOLD) {
-    if (!p.fold_ok) return ADFFT_ERR_NOT_SUPPORTED;
+    if (!p.fold_ok && !p.tp_ok) return ADFFT_ERR_NOT_SUPPORTED;
     p.algo = algo;
     return ADFFT_OK;
   }
@@ -527,20 +683,25 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
     info->residues = p.blu.args.chunks;
     info->fold = 0;
     info->cluster = 1;
+  } else if (!p.fold_ok && p.tp_ok) {
+    info->fft_len = p.tp_A * p.tp_B;      // the sub-FFT length, split A x B over two passes
+    info->residues = p.tp1.args.P;
+    info->fold = p.tp1.args.q;
+    info->cluster = p.tp1.args.C;
   } else {
     info->fft_len = p.fused.args.Np;
     info->residues = p.fused.args.P;
     info->fold = p.fused.args.q;
     info->cluster = p.fused.args.C;
   }
-  info->passes = 1;
+  info->passes = (!p.fold_ok && p.tp_ok && p.algo == ADFFT_ALGO_FOLD) ? 2 : 1;
   info->scale = p.scale;
   return ADFFT_OK;
 }
 
 size_t adfft_plan_workspace_bytes(adfft_plan_t plan) {
-  (void)plan;
-  return 0;
+  if (!plan) return 0;
+  return plan->p.ws_bytes;
 }
 
 int adfft_execute(adfft_plan_t plan, const void* d_in, void* d_out, void* stream) {
@@ -550,9 +711,15 @@ int adfft_execute(adfft_plan_t plan, const void* d_in, void* d_out, void* stream
   if (!aligned16(d_in) || !aligned16(d_out)) return ADFFT_ERR_MISALIGNED;
   if (overlaps(d_in, p.in_bytes(), d_out, p.out_bytes())) return ADFFT_ERR_OVERLAP;
   if (p.batch == 0) return ADFFT_OK;
-  cudaError_t e = (p.algo == ADFFT_ALGO_BLUESTEIN)
-                      ? bluestein_launch(p.blu, d_in, d_out, (cudaStream_t)stream)
-                      : fused_launch(p.fused, d_in, d_out, (cudaStream_t)stream);
+  cudaError_t e;
+  if (p.algo == ADFFT_ALGO_BLUESTEIN) {
+    e = bluestein_launch(p.blu, d_in, d_out, (cudaStream_t)stream);
+  } else if (p.fold_ok) {
+    e = fused_launch(p.fused, d_in, d_out, (cudaStream_t)stream);
+  } else {
+    e = fused_launch(p.tp1, d_in, p.d_ws, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = twopass_launch(p.tp2, p.d_ws, d_out, (cudaStream_t)stream);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_status(e);

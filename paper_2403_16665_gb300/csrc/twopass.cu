@@ -1,0 +1,45 @@
+// Instantiations and launcher of the second pass of the two-pass form.
+#include "adfft_internal.h"
+#include "twopass.cuh"
+
+namespace adfft {
+
+namespace {
+
+using KernelFn = void (*)(const TwoPassArgs);
+
+template <typename V, int VPT>
+KernelFn pick_r0(int r0) {
+  switch (r0) {
+    case 1: return twopass_columns_kernel<V, VPT, 1>;
+    case 2: return twopass_columns_kernel<V, VPT, 2>;
+    case 4: return twopass_columns_kernel<V, VPT, 4>;
+    case 8: return twopass_columns_kernel<V, VPT, 8>;
+    default: return twopass_columns_kernel<V, VPT, 16>;
+  }
+}
+
+KernelFn pick_kernel(const TwoPassLaunch& L) {
+  return L.dbl ? pick_r0<double2, 16>(L.r0) : pick_r0<float2, 32>(L.r0);
+}
+
+}  // namespace
+
+cudaError_t twopass_prepare(const TwoPassLaunch& L) {
+  return cudaFuncSetAttribute(pick_kernel(L), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+cudaError_t twopass_launch(const TwoPassLaunch& L, const void* scratch, void* out, cudaStream_t stream) {
+  TwoPassArgs t = L.args;
+  t.scratch = scratch;
+  t.out = out;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.grid_x, L.grid_y, 1);
+  cfg.blockDim = dim3(L.threads, 1, 1);
+  cfg.dynamicSmemBytes = L.smem;
+  cfg.stream = stream;
+  cfg.numAttrs = 0;
+  return cudaLaunchKernelEx(&cfg, pick_kernel(L), t);
+}
+
+}  // namespace adfft

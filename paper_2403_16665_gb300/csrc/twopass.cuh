@@ -1,0 +1,135 @@
+// Second pass of the two-pass (four-step) form for sub-FFT lengths beyond one
+// cluster's shared memory.
+//
+// With Nc = A B, n = B a + b and m = m1 + R1 m2 (R1 = alpha A, m1 < R1, m2 < B):
+//     U_{m1 + R1 m2} = sum_b W_B^{m2 b} [ W_Mc^{m1 b} V_b[m1] ],
+//     V_b[m1] = sum_a W_{R1}^{m1 a} u_{B a + b}     (an alpha-DFT of column b).
+// The first pass (fused kernel, kColumns mode) writes the bracket to the
+// scratch rows S[b][m1].  This pass runs the length-B DFTs over b for a block
+// of columns m1 and for the mirror columns R1 - m1, and for packed real input
+// unpacks (E_j, O_j) exactly as the single-pass epilogue:
+//     X_j = E_j + W_M^j O_j,  X_{j+Mc} = E_j - W_M^j O_j,  X_{M-j} = conj X_j,
+// where the partner Mc - j of j = m1 + R1 m2 is (R1 - m1) + R1 (B - 1 - m2)
+// (m1 > 0) or R1 ((B - m2) mod B) (m1 = 0).  Consecutive lanes take
+// consecutive m1, so every output row segment is written contiguously.
+#pragma once
+
+#include "fused.cuh"
+
+namespace adfft {
+
+struct TwoPassArgs {
+  FusedArgs f;          // FFT view: Np = B, RPC = 2 W (columns), Mt = B, tw = W_B table, region, nrad
+  const void* scratch;  // [batch][B][R1]
+  void* out;            // [batch][M]
+  long long batch;
+  int B, logB;
+  long long R1;         // row length alpha A
+  long long Mc, M;
+  int W;                // column pairs per CTA
+  int real_packed;
+  const void* wM;       // two-level W_M table (global memory), for the real unpacking
+  int wM_bits, wM_lo_n;
+  double scale;
+};
+
+template <typename V>
+__device__ __forceinline__ V tw_global(const void* t, int lo_n, int bits, unsigned long long e) {
+  const V* lo = reinterpret_cast<const V*>(t);
+  const V* hi = lo + lo_n;
+  return cmul(__ldg(hi + (e >> bits)), __ldg(lo + (e & ((1ull << bits) - 1))));
+}
+
+template <typename V, int VPT, int R0>
+__global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs t) {
+  using Rl = typename real_of<V>::type;
+  const FusedArgs& a = t.f;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tw_n = a.tw_lo_n + a.tw_hi_n;
+  const FusedSmem L = fused_smem_layout(tw_n, 0, a.RPC, a.region, (int)sizeof(V));
+  V* tw_s = reinterpret_cast<V*>(smem_raw + L.tw);
+  V* buf = reinterpret_cast<V*>(smem_raw + L.buf);
+  for (int i = threadIdx.x; i < tw_n; i += blockDim.x) tw_s[i] = reinterpret_cast<const V*>(a.tw)[i];
+  __syncthreads();
+  TwTable<V> tab{tw_s, tw_s + a.tw_lo_n, a.tw_bits, (1u << a.tw_bits) - 1u};
+
+  const unsigned B = (unsigned)t.B;
+  const unsigned W = (unsigned)t.W;
+  const unsigned long long R1 = (unsigned long long)t.R1;
+  const unsigned long long Mc = (unsigned long long)t.Mc;
+  const unsigned npairs = (unsigned)(t.real_packed ? R1 / 2 + 1 : R1);
+  const unsigned p0 = blockIdx.x * W;
+  const unsigned np = min(W, npairs - p0);
+  const unsigned T = blockDim.x;
+  const Rl S = (Rl)t.scale;
+
+  for (long long sig = blockIdx.y; sig < t.batch; sig += gridDim.y) {
+    const V* src = reinterpret_cast<const V*>(t.scratch) + (size_t)sig * B * R1;
+    // columns 0..W-1: m1 = p0 + w;  W..2W-1: the mirrors (R1 - m1) mod R1
+    const unsigned ncol = t.real_packed ? 2 * W : W;
+    for (unsigned idx = threadIdx.x; idx < ncol * B; idx += T) {
+      const unsigned w = idx % ncol, b = idx / ncol;   // consecutive threads: consecutive columns
+      V v = czero<V>();
+      const unsigned pw = (w < W) ? w : w - W;
+      if (pw < np) {
+        const unsigned long long m1 = p0 + pw;
+        const unsigned long long col = (w < W) ? m1 : (R1 - m1) % R1;
+        v = __ldg(src + (size_t)b * R1 + col);
+      }
+      buf[w * a.region + pad16((int)b)] = v;
+    }
+    __syncthreads();
+    {
+      int Ns = 1, logNs = 0;
+      constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : 4;
+      if constexpr (R0 > 1) {
+        stockham_pass<R0, VPT, V>(a, buf, tab, Ns, logNs);
+        Ns = R0;
+        logNs = LOGR0;
+      }
+      for (int p = 1; p < a.nrad; ++p) {
+        stockham_pass<16, VPT, V>(a, buf, tab, Ns, logNs);
+        Ns <<= 4;
+        logNs += 4;
+      }
+    }
+    V* out = reinterpret_cast<V*>(t.out) + (size_t)sig * t.M;
+    if (t.real_packed) {
+      // item (pair w, m2): j = m1 + R1 m2 and its partner in the mirror column
+      for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
+        const unsigned w = idx % W, m2 = idx / W;
+        if (w >= np) continue;
+        const unsigned long long m1 = p0 + w;
+        // columns 0 and R1/2 pair with themselves: only half of their m2 are leaders
+        const bool self = (m1 == 0) || (2 * m1 == R1);
+        if (self && 2 * m2 > B) continue;
+        if (self && m1 != 0 && 2 * m2 == B) continue;
+        const unsigned m2p = (m1 == 0) ? (B - m2) & (B - 1) : B - 1 - m2;
+        const V Uj = buf[w * a.region + pad16((int)m2)];
+        const V Up = buf[(W + w) * a.region + pad16((int)m2p)];
+        const unsigned long long j = m1 + R1 * m2;
+        const V E = cscale(cadd(Uj, cconj(Up)), (Rl)0.5);
+        const V O = cscale(cmul_mi(csub(Uj, cconj(Up))), (Rl)0.5);
+        const V wO = cmul(tw_global<V>(t.wM, t.wM_lo_n, t.wM_bits, j), O);
+        const V X1 = cscale(cadd(E, wO), S);
+        const V X2 = cscale(csub(E, wO), S);
+        out[j] = X1;
+        out[j + Mc] = X2;
+        if (j != 0 && 2 * j != Mc) {
+          out[Mc - j] = cconj(X2);
+          out[(unsigned long long)t.M - j] = cconj(X1);
+        }
+      }
+    } else {
+      for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
+        const unsigned w = idx % W, m2 = idx / W;
+        if (w >= np) continue;
+        const unsigned long long j = p0 + w + R1 * m2;
+        out[j] = cscale(buf[w * a.region + pad16((int)m2)], S);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace adfft

@@ -1,0 +1,90 @@
+"""GPU parity of the two-pass (four-step) form used when the sub-FFT length
+exceeds one cluster's shared memory, against the FP64 oracle on sampled bins."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_16665_gb300 import adfft, signals
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    adfft.load()
+    return torch
+
+
+def tol_for(M, dbl):
+    return 1e-12 if dbl else 2e-6 * max(1.0, np.log2(M))
+
+
+NP = {adfft.R32: np.float32, adfft.R64: np.float64, adfft.C64: np.complex64, adfft.C128: np.complex128}
+
+
+def run(torch, x, M, code):
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    B, N = xt.shape
+    plan = adfft.Plan(N, batch=B, dtype=code, M=M)
+    dbl = code in (adfft.R64, adfft.C128)
+    X = torch.empty((B, M), dtype=torch.complex128 if dbl else torch.complex64, device=dev)
+    plan.execute(xt.data_ptr(), X.data_ptr())
+    plan.sync_status()
+    return X, plan
+
+
+def sample_bins(M, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([np.arange(8), M - 1 - np.arange(8), [M // 2 - 1, M // 2, M // 2 + 1],
+                                     rng.integers(0, M, n)]))
+
+
+@pytest.mark.parametrize("code", [adfft.R32, adfft.C64, adfft.R64, adfft.C128])
+@pytest.mark.parametrize("N,alpha", [(1 << 15, 2), (1 << 16, 4), (1 << 17, 8), (1 << 16, 2.5),
+                                     (1 << 18, 16), (1 << 15, 3)])
+def test_two_pass_sampled(code, N, alpha):
+    torch = _torch()
+    M = int(round(alpha * N))
+    rng = np.random.default_rng(N + M)
+    x = rng.standard_normal((2, N))
+    if code in (adfft.C64, adfft.C128):
+        x = x + 1j * rng.standard_normal((2, N))
+    x = x.astype(NP[code])
+    X, plan = run(torch, x, M, code)
+    real = code in (adfft.R32, adfft.R64)
+    Nc, Mc = (N // 2, M // 2) if real else (N, M)
+    limit = 8192 if code in (adfft.R64, adfft.C128) else 16384
+    expect = 2 if np.gcd(Nc, Mc) > limit else 1
+    assert plan.info.passes == expect, (plan.info.passes, plan.info.fft_len)
+    assert (plan.workspace_bytes() > 0) == (expect == 2)
+    bins = sample_bins(M, 600, N)
+    got = X[:, torch.from_numpy(bins).cuda()].cpu().numpy()
+    ref = oracle.alpha_dft(x.astype(np.complex128), M, bins=bins)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= tol_for(M, code in (adfft.R64, adfft.C128)), err.max()
+    if code in (adfft.R32, adfft.R64):
+        Xs = X[0].cpu().numpy()
+        m = np.arange(1, M)
+        assert np.max(np.abs(Xs[M - m] - np.conj(Xs[m]))) <= 1e-5 * np.max(np.abs(Xs))
+
+
+def test_large_real_workload_sampled():
+    """8 real fp32 signals, N = 2^22, alpha = 16 (2^26 bins each): 2 signals on
+    sampled bins, including windows around the strongest tones."""
+    torch = _torch()
+    x, prm = signals.large_r32()
+    N, M = 1 << 22, 1 << 26
+    X, plan = run(torch, x, M, adfft.R32)
+    assert plan.info.passes == 2
+    for s in (0, 7):
+        top = np.argsort(prm["A"][s])[-3:]
+        centers = np.round(prm["nu"][s, top] * 16).astype(np.int64)
+        win = (centers[:, None] + np.arange(-8, 9)[None, :]).ravel() % M
+        bins = np.unique(np.concatenate([win, sample_bins(M, 160, s)]))
+        got = X[s, torch.from_numpy(bins).cuda()].cpu().numpy()
+        ref = oracle.alpha_dft(x[s].astype(np.float64), M, bins=bins)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= tol_for(M, False), err
