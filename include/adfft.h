@@ -194,6 +194,43 @@ int adfft_plan_sync_status(adfft_plan_t plan, void *stream);
  */
 int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *stream);
 
+/*
+ * Forward transform that allocates no device memory.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc at the point where they need the transform:
+ * code running while a CUDA graph is being captured (an allocation there
+ * would be captured or rejected), code whose device memory is entirely
+ * owned by another allocator or a fixed pool, and latency-critical loops
+ * where an allocation could block.  Such callers cannot create a plan
+ * (plan creation allocates tables and workspace), so this call takes the
+ * sizes directly and returns when the work is queued on `stream`.
+ *
+ * Arguments: N samples and M = alpha*N bins per signal, `batch` signals,
+ * dtype ADFFT_R32 or ADFFT_C64 (others: ADFFT_ERR_NOT_SUPPORTED); d_in
+ * [batch][N] and d_out [batch][M] complex64 device buffers owned by the
+ * caller, 16-byte aligned and not overlapping; scale S = 1/N.  The result
+ * is the same transform as adfft_execute, computed with the two-pass
+ * (four-step) form.
+ *
+ * Storage: the pass-1 intermediate and the twiddle tables live in one fixed
+ * static device array of the library (1 MiB of tables + 32 MiB of scratch),
+ * which every GPU that loads the library keeps until the process exits.
+ * Limits: N/2 (real) or N (complex) a power of two >= 4, real input with
+ * even N and M, batch * M/2 (real) or batch * M (complex) complex64 values
+ * within the 32 MiB scratch, M < 2^30; larger requests return
+ * ADFFT_ERR_UNSUPPORTED_SIZE without launching anything.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once for that device; make that first call before
+ * any stream capture begins.  Every call reuses the same array and leaves the
+ * last call's contents in it; nothing in it needs to start at zero.  Calls
+ * whose work overlaps on the GPU (for example on two streams) race on the
+ * array and produce wrong results: serialise them.
+ */
+int adfft_execute_noalloc(int64_t N, int64_t M, int64_t batch, int dtype, const void *d_in,
+                          void *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

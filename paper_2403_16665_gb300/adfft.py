@@ -34,6 +34,7 @@ EXPORTS = (
     "adfft_plan_set_scale", "adfft_plan_set_algorithm", "adfft_plan_set_precision",
     "adfft_plan_get_info", "adfft_plan_workspace_bytes", "adfft_execute",
     "adfft_execute_adjoint", "adfft_execute_host", "adfft_plan_sync_status",
+    "adfft_execute_noalloc",
 )
 
 
@@ -80,6 +81,7 @@ def load(path: str | None = None):
         "adfft_execute_adjoint": ([vp, vp, vp, vp], i32),
         "adfft_execute_host": ([vp, vp, vp, vp], i32),
         "adfft_plan_sync_status": ([vp, vp], i32),
+        "adfft_execute_noalloc": ([i64, i64, i64, i32, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -171,6 +173,13 @@ class Plan:
             self.destroy()
         except Exception:
             pass
+
+
+def execute_noalloc(N, M, batch, dtype, d_in: int, d_out: int, stream=None):
+    """adfft_execute_noalloc: forward transform with no device allocation (R32 / C64)."""
+    _check(load().adfft_execute_noalloc(int(N), int(M), int(batch), int(dtype), ctypes.c_void_p(d_in),
+                                        ctypes.c_void_p(d_out), ctypes.c_void_p(_stream_handle(stream))),
+           "adfft_execute_noalloc")
 
 
 def _dtype_code(t):
