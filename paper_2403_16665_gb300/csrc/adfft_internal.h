@@ -12,7 +12,11 @@
 #include "bluestein.cuh"
 #include "twopass.cuh"
 
+struct adfft_plan_s;
+
 namespace adfft {
+
+constexpr int kRaggedStreams = 4;   // side streams a ragged plan's graph forks over
 
 // Launch geometry of the fused single-pass kernel.
 struct FusedLaunch {
@@ -80,6 +84,18 @@ struct Plan {
   void* d_ws = nullptr;               // scratch [batch][B][R1]
   size_t ws_bytes = 0;
 
+  // ragged plan: one uniform sub-plan per (N, M) shape class, all launched from one CUDA graph
+  bool ragged = false;
+  int64_t r_count = 0;
+  std::vector<int64_t> r_in_off, r_out_off;    // count + 1 packed offsets
+  std::vector<adfft_plan_s*> r_sub;             // sub-plans (own their tables and workspace)
+  std::vector<void*> r_offs;                    // per class: device {in, out} offsets of its signals
+  cudaStream_t r_streams[kRaggedStreams] = {};
+  cudaEvent_t r_fork = nullptr, r_join[kRaggedStreams] = {};
+  cudaGraphExec_t r_graph[2] = {nullptr, nullptr};   // forward, adjoint
+  const void* r_graph_in[2] = {nullptr, nullptr};
+  void* r_graph_out[2] = {nullptr, nullptr};
+
   // host-memory staging of adfft_execute_host
   void* d_stage_in = nullptr;
   void* d_stage_out = nullptr;
@@ -102,9 +118,20 @@ cudaError_t adjoint_prepare(const FusedLaunch& L);
 cudaError_t adjoint_launch(const FusedLaunch& L, const void* g, void* xb, cudaStream_t stream);
 size_t adjoint_smem_bytes(const FusedLaunch& L);
 
+// Launch the plan's forward / adjoint kernels (no argument checks).
+int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s);
+int launch_adjoint(Plan& p, const void* g, void* xb, cudaStream_t s);
+int cuda_status_of(cudaError_t e);
+
+// Ragged plans (ragged.cu).
+adfft_plan_s* ragged_create(const int64_t* N, const double* alpha, int64_t count, int dtype, int* err);
+int ragged_execute(Plan& p, const void* in, void* out, cudaStream_t s, int which);
+void ragged_release(Plan& p);
+
 // Two-pass second-pass launchers (twopass.cu).
 cudaError_t twopass_prepare(const TwoPassLaunch& L);
 cudaError_t twopass_launch(const TwoPassLaunch& L, const void* scratch, void* out, cudaStream_t stream);
+cudaError_t twopass_adjoint_launch(const TwoPassLaunch& L, const void* g, void* scratch, cudaStream_t stream);
 
 // Chirp-z launchers (bluestein.cu).
 cudaError_t bluestein_prepare(const BluesteinLaunch& L);

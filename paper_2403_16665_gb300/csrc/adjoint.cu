@@ -26,12 +26,14 @@ KernelFn pick_kernel(const FusedLaunch& L) {
     switch (L.mode) {
       case kLoadComplex: return pick_r0<double2, kLoadComplex, 16>(L.r0);
       case kLoadRealPacked: return pick_r0<double2, kLoadRealPacked, 16>(L.r0);
+      case kColumns: return pick_r0<double2, kColumns, 16>(L.r0);
       default: return pick_r0<double2, kLoadRealPlain, 16>(L.r0);
     }
   }
   switch (L.mode) {
     case kLoadComplex: return pick_r0<float2, kLoadComplex, 32>(L.r0);
     case kLoadRealPacked: return pick_r0<float2, kLoadRealPacked, 32>(L.r0);
+    case kColumns: return pick_r0<float2, kColumns, 32>(L.r0);
     default: return pick_r0<float2, kLoadRealPlain, 32>(L.r0);
   }
 }

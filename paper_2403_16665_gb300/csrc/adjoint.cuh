@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
   const unsigned n1 = min(Nc, n0 + per);
 
   for (long long sig = blockIdx.y; sig < a.batch; sig += gridDim.y) {
-    const V* g = reinterpret_cast<const V*>(a.in) + sig * a.M;
+    const V* g = reinterpret_cast<const V*>(a.in) + ((MODE == kColumns) ? sig * a.M : sig_out_off(a, sig));
 
     // ---- prologue: conj of the CTA's residues of the (folded) spectrum, natural order
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
@@ -133,10 +133,14 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
         }
       }
       acc = cscale(acc, S);
+      unsigned char* obase = reinterpret_cast<unsigned char*>(a.out);
       if (MODE == kLoadRealPlain) {
-        reinterpret_cast<Rl*>(a.out)[sig * (long long)a.in_stride + n] = acc.x;
+        reinterpret_cast<Rl*>(obase + sig_in_bytes(a, sig))[n] = acc.x;
+      } else if (MODE == kColumns) {
+        // transpose of the two-pass first pass: column (sig mod cols) of the core, stride cols
+        reinterpret_cast<V*>(obase + sig_in_bytes(a, sig / a.cols))[(sig % a.cols) + (long long)n * a.cols] = acc;
       } else {
-        reinterpret_cast<V*>(a.out)[sig * (long long)Nc + n] = acc;
+        reinterpret_cast<V*>(obase + sig_in_bytes(a, sig))[n] = acc;
       }
     }
     if (a.C > 1) cluster_arrive(); else __syncthreads();

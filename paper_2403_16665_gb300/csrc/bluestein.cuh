@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(512) bluestein_kernel(const BluesteinArgs b) {
       V v = czero<V>();
       if ((long long)i < b.N) {
         V x;
-        if (b.real_in) x = cmake<V>(__ldg(reinterpret_cast<const Rl*>(a.in) + sig * b.N + i), (Rl)0);
-        else x = __ldg(reinterpret_cast<const V*>(a.in) + sig * b.N + i);
+        const unsigned char* base = reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, sig);
+        if (b.real_in) x = cmake<V>(__ldg(reinterpret_cast<const Rl*>(base) + i), (Rl)0);
+        else x = __ldg(reinterpret_cast<const V*>(base) + i);
         v = cmul(x, __ldg(chirp + i));
       }
       buf[pad16((int)i)] = v;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(512) bluestein_kernel(const BluesteinArgs b) {
     }
     __syncthreads();
     run_all_passes<V, VPT, R0>(a, buf, tab);
-    V* out = reinterpret_cast<V*>(a.out) + sig * a.M + m0;
+    V* out = reinterpret_cast<V*>(a.out) + sig_out_off(a, sig) + m0;
     for (int t = threadIdx.x; t < nb; t += T) {
       const V y = cconj(buf[pad16(t + (int)b.N - 1)]);
       out[t] = cscale(cmul(y, __ldg(chirp + m0 + t)), S);

@@ -60,6 +60,11 @@ struct FusedArgs {
   int stage_bytes;       // > 0: each signal's input is bulk-copied into shared memory first
   int* status;           // device status word of the plan
   FastDiv divP, divRPC;
+  // per-signal placement for packed (ragged) batches: offs[2 s] = byte offset of
+  // signal s in the input, offs[2 s + 1] = its first output bin; NULL means
+  // s * in_stride * in_unit bytes and s * M bins
+  const long long* offs;
+  int in_unit;           // bytes per in_stride unit (real scalar or complex element)
   // kColumns only: columns per signal, and the two-level table of W_Mpost (global memory)
   long long cols;
   const void* post_tw;
@@ -79,6 +84,13 @@ __host__ __device__ inline FusedSmem fused_smem_layout(int tw_n, int stage_bytes
   s.buf = s.stage + ((stage_bytes + 15) & ~15);
   s.total = s.buf + rpc * region * esz;
   return s;
+}
+
+__device__ __forceinline__ long long sig_in_bytes(const FusedArgs& a, long long s) {
+  return a.offs ? a.offs[2 * s] : s * a.in_stride * a.in_unit;
+}
+__device__ __forceinline__ long long sig_out_off(const FusedArgs& a, long long s) {
+  return a.offs ? a.offs[2 * s + 1] : s * a.M;
 }
 
 template <typename V>
@@ -304,14 +316,13 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   const Rl S = (Rl)a.scale;
   constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : 4;
   constexpr int kEpilogueUnroll = epilogue_unroll<V, MODE>();
-  const size_t in_bytes_per_sig = (MODE == kLoadComplex ? sizeof(V) : sizeof(Rl)) * (size_t)a.in_stride;
   uint32_t phase = 0, fail_phase = 0;
   bool failed = false;
 
   // prefetch the first signal's input
   if (staged && threadIdx.x == 0 && (long long)blockIdx.y < a.batch) {
     mbar_arrive_expect_tx(bar, (uint32_t)a.stage_bytes);
-    bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + blockIdx.y * in_bytes_per_sig,
+    bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, blockIdx.y),
                   (uint32_t)a.stage_bytes, bar);
   }
 
@@ -326,11 +337,12 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
       }
       phase ^= 1u;
     } else if (MODE == kColumns) {
-      u = reinterpret_cast<const V*>(a.in) + (sig / a.cols) * a.in_stride + (sig % a.cols);
+      u = reinterpret_cast<const V*>(reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, sig / a.cols)) +
+          (sig % a.cols);
     } else {
-      u = reinterpret_cast<const unsigned char*>(a.in) + sig * in_bytes_per_sig;
+      u = reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, sig);
     }
-    V* out = reinterpret_cast<V*>(a.out) + sig * a.M;
+    V* out = reinterpret_cast<V*>(a.out) + ((MODE == kColumns) ? sig * a.M : sig_out_off(a, sig));
     const unsigned col = (MODE == kColumns) ? (unsigned)(sig % a.cols) : 0u;
 
     // ---- K1: fold + residue twiddle + first radix
@@ -343,7 +355,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     if (staged && threadIdx.x == 0 && nxt < a.batch && !failed) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(bar, (uint32_t)a.stage_bytes);
-      bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + nxt * in_bytes_per_sig,
+      bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, nxt),
                     (uint32_t)a.stage_bytes, bar);
     }
 

@@ -188,6 +188,7 @@ extern "C" int adfft_execute_noalloc(int64_t N, int64_t M, int64_t batch, int dt
       a.stage_bytes = 0;
       a.status = nullptr;
       a.cols = B;
+      a.in_unit = 8;
       a.Mpost = Mc;
       const int lr0 = (a.logNp == 0) ? 0 : (a.logNp % 4 ? a.logNp % 4 : 4);
       a.nrad = 1 + (a.logNp - lr0) / 4;

@@ -139,6 +139,7 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   a.stage_bytes = stage;
   a.status = status;
   a.cols = 1;
+  a.in_unit = (mode == kLoadComplex || mode == kColumns) ? (int)esz : (int)(esz / 2);
   // passes: a first pass of radix R0 = 2^(log2 Np mod 4) (16 if that is 0), then radix 16
   const int L2 = a.logNp;
   int lr0 = (L2 == 0) ? 0 : (L2 % 4 ? L2 % 4 : 4);
@@ -179,7 +180,7 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   L.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(batch, 65535));
   L.smem = smem;
   e = fused_prepare(L);
-  if (e == cudaSuccess && mode != kColumns) e = adjoint_prepare(L);
+  if (e == cudaSuccess) e = adjoint_prepare(L);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_status(e);
@@ -216,6 +217,7 @@ int setup_fold(Plan& p) {
                            p.fused, &p.d_tw);
   if (rc != ADFFT_OK) return rc;
   p.fused.args.in_stride = p.N;   // complex elements or real scalars per signal
+  p.fused.args.in_unit = (int)p.in_elem;
   p.fused.args.M = p.M;
   p.fold_ok = true;
   return ADFFT_OK;
@@ -475,6 +477,8 @@ int setup_bluestein(Plan& p) {
   const int lr0 = (L2 == 0) ? 0 : (L2 % 4 ? L2 % 4 : 4);
   a.nrad = 1 + (L2 - lr0) / 4;
   a.status = p.d_status;
+  a.in_stride = p.N;
+  a.in_unit = (int)p.in_elem;
   b.chirp = p.d_chirp;
   b.H = p.d_H;
   b.N = p.N;
@@ -495,7 +499,49 @@ int setup_bluestein(Plan& p) {
   return ADFFT_OK;
 }
 
+}  // namespace
+
+int cuda_status_of(cudaError_t e) { return cuda_status(e); }
+
+int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s) {
+  cudaError_t e;
+  if (p.algo == ADFFT_ALGO_BLUESTEIN) {
+    e = bluestein_launch(p.blu, in, out, s);
+  } else if (p.fold_ok) {
+    e = fused_launch(p.fused, in, out, s);
+  } else {
+    e = fused_launch(p.tp1, in, p.d_ws, s);
+    if (e == cudaSuccess) e = twopass_launch(p.tp2, p.d_ws, out, s);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  return ADFFT_OK;
+}
+
+int launch_adjoint(Plan& p, const void* g, void* xb, cudaStream_t s) {
+  cudaError_t e;
+  if (p.fold_ok) {
+    e = adjoint_launch(p.fused, g, xb, s);
+  } else if (p.tp_ok) {
+    // transpose of the two passes, in reverse order, through the same workspace
+    e = twopass_adjoint_launch(p.tp2, g, p.d_ws, s);
+    if (e == cudaSuccess) e = adjoint_launch(p.tp1, p.d_ws, xb, s);
+  } else {
+    return ADFFT_ERR_NOT_SUPPORTED;   // the chirp-z form has no adjoint kernel
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  return ADFFT_OK;
+}
+
+namespace {
+
 void release(Plan& p) {
+  if (p.ragged) ragged_release(p);
   for (void** q : {&p.d_blu_tw, &p.d_chirp, &p.d_H, &p.d_tp_tw1, &p.d_tp_post, &p.d_tp_tw2, &p.d_tp_wM, &p.d_ws}) {
     if (*q) cudaFree(*q);
     *q = nullptr;
@@ -604,16 +650,23 @@ adfft_plan_t adfft_plan_create(int64_t N, double alpha, int64_t batch, int dtype
 }
 
 adfft_plan_t adfft_plan_create_ragged(const int64_t* N, const double* alpha, int64_t count, int dtype) {
-  (void)N;
-  (void)alpha;
-  (void)count;
-  (void)dtype;
-  return adfft::fail(ADFFT_ERR_NOT_SUPPORTED, nullptr);
+  int err = ADFFT_OK;
+  adfft_plan_s* h = adfft::ragged_create(N, alpha, count, dtype, &err);
+  if (!h) return adfft::fail(err, nullptr);
+  adfft::g_last_error = ADFFT_OK;
+  return h;
 }
 
 int adfft_plan_offsets(adfft_plan_t plan, int64_t* in_off, int64_t* out_off) {
   if (!plan) return ADFFT_ERR_INVALID_ARG;
   const Plan& p = plan->p;
+  if (p.ragged) {
+    for (int64_t i = 0; i <= p.r_count; ++i) {
+      if (in_off) in_off[i] = p.r_in_off[(size_t)i];
+      if (out_off) out_off[i] = p.r_out_off[(size_t)i];
+    }
+    return ADFFT_OK;
+  }
   for (int64_t i = 0; i <= p.batch; ++i) {
     if (in_off) in_off[i] = i * p.N;
     if (out_off) out_off[i] = i * p.M;
@@ -632,6 +685,7 @@ int adfft_plan_destroy(adfft_plan_t plan) {
 
 int adfft_plan_set_scale(adfft_plan_t plan, double S) {
   if (!plan || !isfinite(S)) return ADFFT_ERR_INVALID_ARG;
+  if (plan->p.ragged) return ADFFT_ERR_NOT_SUPPORTED;   // each ragged signal keeps S = 1/N_i
   plan->p.scale = S;
   plan->p.fused.args.scale = S;
   plan->p.blu.args.f.scale = S;
@@ -642,6 +696,7 @@ int adfft_plan_set_scale(adfft_plan_t plan, double S) {
 int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
   if (!plan) return ADFFT_ERR_INVALID_ARG;
   Plan& p = plan->p;
+  if (p.ragged) return (algo == ADFFT_ALGO_AUTO) ? ADFFT_OK : ADFFT_ERR_NOT_SUPPORTED;
   if (algo == ADFFT_ALGO_AUTO) {
     p.algo = (p.fold_ok || p.tp_ok) ? ADFFT_ALGO_FOLD : ADFFT_ALGO_BLUESTEIN;
     return ADFFT_OK;
@@ -678,6 +733,18 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
   info->batch = p.batch;
   info->dtype = p.dtype;
   info->algo = p.algo;
+  if (p.ragged) {
+    info->batch = p.r_count;
+    info->fft_len = 0;
+    info->residues = (int64_t)p.r_sub.size();   // shape classes
+    info->fold = 0;
+    info->cluster = 0;
+    int passes = 1;
+    for (auto* sp : p.r_sub) passes = std::max(passes, (!sp->p.fold_ok && sp->p.tp_ok) ? 2 : 1);
+    info->passes = passes;
+    info->scale = 0.0;
+    return ADFFT_OK;
+  }
   if (p.algo == ADFFT_ALGO_BLUESTEIN) {
     info->fft_len = p.blu.args.f.Np;
     info->residues = p.blu.args.chunks;
@@ -701,7 +768,9 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
 
 size_t adfft_plan_workspace_bytes(adfft_plan_t plan) {
   if (!plan) return 0;
-  return plan->p.ws_bytes;
+  size_t total = plan->p.ws_bytes;
+  for (auto* sp : plan->p.r_sub) total += sp->p.ws_bytes;
+  return total;
 }
 
 int adfft_execute(adfft_plan_t plan, const void* d_in, void* d_out, void* stream) {
@@ -710,21 +779,9 @@ int adfft_execute(adfft_plan_t plan, const void* d_in, void* d_out, void* stream
   Plan& p = plan->p;
   if (!aligned16(d_in) || !aligned16(d_out)) return ADFFT_ERR_MISALIGNED;
   if (overlaps(d_in, p.in_bytes(), d_out, p.out_bytes())) return ADFFT_ERR_OVERLAP;
+  if (p.ragged) return ragged_execute(p, d_in, d_out, (cudaStream_t)stream, 0);
   if (p.batch == 0) return ADFFT_OK;
-  cudaError_t e;
-  if (p.algo == ADFFT_ALGO_BLUESTEIN) {
-    e = bluestein_launch(p.blu, d_in, d_out, (cudaStream_t)stream);
-  } else if (p.fold_ok) {
-    e = fused_launch(p.fused, d_in, d_out, (cudaStream_t)stream);
-  } else {
-    e = fused_launch(p.tp1, d_in, p.d_ws, (cudaStream_t)stream);
-    if (e == cudaSuccess) e = twopass_launch(p.tp2, p.d_ws, d_out, (cudaStream_t)stream);
-  }
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cuda_status(e);
-  }
-  return ADFFT_OK;
+  return launch_forward(p, d_in, d_out, (cudaStream_t)stream);
 }
 
 int adfft_execute_adjoint(adfft_plan_t plan, const void* d_grad_out, void* d_grad_in, void* stream) {
@@ -733,14 +790,9 @@ int adfft_execute_adjoint(adfft_plan_t plan, const void* d_grad_out, void* d_gra
   Plan& p = plan->p;
   if (!aligned16(d_grad_out) || !aligned16(d_grad_in)) return ADFFT_ERR_MISALIGNED;
   if (overlaps(d_grad_out, p.out_bytes(), d_grad_in, p.in_bytes())) return ADFFT_ERR_OVERLAP;
+  if (p.ragged) return ragged_execute(p, d_grad_out, d_grad_in, (cudaStream_t)stream, 1);
   if (p.batch == 0) return ADFFT_OK;
-  if (!p.fold_ok) return ADFFT_ERR_NOT_SUPPORTED;   // the adjoint kernel uses the fold decomposition
-  cudaError_t e = adjoint_launch(p.fused, d_grad_out, d_grad_in, (cudaStream_t)stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cuda_status(e);
-  }
-  return ADFFT_OK;
+  return launch_adjoint(p, d_grad_out, d_grad_in, (cudaStream_t)stream);
 }
 
 int adfft_execute_host(adfft_plan_t plan, const void* h_in, void* h_out, void* stream) {

@@ -23,10 +23,45 @@ KernelFn pick_kernel(const TwoPassLaunch& L) {
   return L.dbl ? pick_r0<double2, 16>(L.r0) : pick_r0<float2, 32>(L.r0);
 }
 
+template <typename V, int VPT>
+KernelFn pick_adj_r0(int r0) {
+  switch (r0) {
+    case 1: return twopass_adjoint_columns_kernel<V, VPT, 1>;
+    case 2: return twopass_adjoint_columns_kernel<V, VPT, 2>;
+    case 4: return twopass_adjoint_columns_kernel<V, VPT, 4>;
+    case 8: return twopass_adjoint_columns_kernel<V, VPT, 8>;
+    default: return twopass_adjoint_columns_kernel<V, VPT, 16>;
+  }
+}
+
+KernelFn pick_adj_kernel(const TwoPassLaunch& L) {
+  return L.dbl ? pick_adj_r0<double2, 16>(L.r0) : pick_adj_r0<float2, 32>(L.r0);
+}
+
 }  // namespace
 
 cudaError_t twopass_prepare(const TwoPassLaunch& L) {
-  return cudaFuncSetAttribute(pick_kernel(L), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(pick_kernel(L), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pick_adj_kernel(L), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e;
+}
+
+// Adjoint of the second pass: spectrum g -> scratch rows.  One CTA per block of
+// W columns out of all R1 (no mirror pairing); the adjoint uses only the first W
+// column regions of the launch's shared-memory layout.
+cudaError_t twopass_adjoint_launch(const TwoPassLaunch& L, const void* g, void* scratch, cudaStream_t stream) {
+  TwoPassArgs t = L.args;
+  t.out = const_cast<void*>(g);
+  t.scratch = scratch;
+  t.f.RPC = t.W;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((t.R1 + t.W - 1) / t.W), L.grid_y, 1);
+  cfg.blockDim = dim3(L.threads, 1, 1);
+  cfg.dynamicSmemBytes = L.smem;
+  cfg.stream = stream;
+  cfg.numAttrs = 0;
+  return cudaLaunchKernelEx(&cfg, pick_adj_kernel(L), t);
 }
 
 cudaError_t twopass_launch(const TwoPassLaunch& L, const void* scratch, void* out, cudaStream_t stream) {

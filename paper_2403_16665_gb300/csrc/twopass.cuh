@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
         logNs += 4;
       }
     }
-    V* out = reinterpret_cast<V*>(t.out) + (size_t)sig * t.M;
+    V* out = reinterpret_cast<V*>(t.out) + (t.f.offs ? t.f.offs[2 * sig + 1] : sig * t.M);
     if (t.real_packed) {
       // item (pair w, m2): j = m1 + R1 m2 and its partner in the mirror column
       for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
@@ -127,6 +127,88 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
         const unsigned long long j = p0 + w + R1 * m2;
         out[j] = cscale(buf[w * a.region + pad16((int)m2)], S);
       }
+    }
+    __syncthreads();
+  }
+}
+
+// Adjoint of the second pass (first step of the two-pass adjoint): for a block
+// of W columns m1, forms the (Hermitian-folded, for packed real input)
+// spectrum ub_{m1 + R1 m2}, runs the inverse B-point DFT over m2 as
+// conj(FFT(conj(.))), multiplies by conj(W_Mc^{m1 b}) and the scale S, and
+// writes scratch row b.  The first pass's adjoint (adjoint kernel, kColumns
+// mode) then takes the rows to the input samples u_{B a + b}.
+//   t.out     : the spectrum g [batch][M] (read), offsets from t.f.offs
+//   t.scratch : [batch][B][R1] (written)
+template <typename V, int VPT, int R0>
+__global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoPassArgs t) {
+  using Rl = typename real_of<V>::type;
+  const FusedArgs& a = t.f;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tw_n = a.tw_lo_n + a.tw_hi_n;
+  const FusedSmem L = fused_smem_layout(tw_n, 0, a.RPC, a.region, (int)sizeof(V));
+  V* tw_s = reinterpret_cast<V*>(smem_raw + L.tw);
+  V* buf = reinterpret_cast<V*>(smem_raw + L.buf);
+  for (int i = threadIdx.x; i < tw_n; i += blockDim.x) tw_s[i] = reinterpret_cast<const V*>(a.tw)[i];
+  __syncthreads();
+  TwTable<V> tab{tw_s, tw_s + a.tw_lo_n, a.tw_bits, (1u << a.tw_bits) - 1u};
+
+  const unsigned B = (unsigned)t.B;
+  const unsigned W = (unsigned)t.W;
+  const unsigned long long R1 = (unsigned long long)t.R1;
+  const unsigned long long Mc = (unsigned long long)t.Mc;
+  const unsigned long long M = (unsigned long long)t.M;
+  const unsigned long long sM = M / Mc;   // W_Mc^e = W_M^{sM e}
+  const unsigned p0 = blockIdx.x * W;
+  const unsigned np = (unsigned)min((unsigned long long)W, R1 - p0);
+  const unsigned T = blockDim.x;
+  const Rl S = (Rl)t.scale;
+
+  for (long long sig = blockIdx.y; sig < t.batch; sig += gridDim.y) {
+    const V* g = reinterpret_cast<const V*>(t.out) + (t.f.offs ? t.f.offs[2 * sig + 1] : sig * t.M);
+    for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
+      const unsigned w = idx % W, m2 = idx / W;
+      V v = czero<V>();
+      if (w < np) {
+        const unsigned long long j = p0 + w + R1 * m2;
+        if (t.real_packed) {
+          const V g0 = __ldg(g + j);
+          const V g1 = __ldg(g + j + Mc);
+          const V g2 = __ldg(g + (M - j) % M);
+          const V g3 = __ldg(g + (Mc - j));
+          const V h0 = cscale(cadd(g0, cconj(g2)), (Rl)0.5);
+          const V h1 = cscale(cadd(g1, cconj(g3)), (Rl)0.5);
+          const V d = cmulc(csub(h0, h1), tw_global<V>(t.wM, t.wM_lo_n, t.wM_bits, j));
+          v = cadd(cadd(h0, h1), cmul_pi(d));
+        } else {
+          v = __ldg(g + j);
+        }
+      }
+      buf[w * a.region + pad16((int)m2)] = cconj(v);
+    }
+    __syncthreads();
+    {
+      int Ns = 1, logNs = 0;
+      constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : 4;
+      if constexpr (R0 > 1) {
+        stockham_pass<R0, VPT, V>(a, buf, tab, Ns, logNs);
+        Ns = R0;
+        logNs = LOGR0;
+      }
+      for (int p = 1; p < a.nrad; ++p) {
+        stockham_pass<16, VPT, V>(a, buf, tab, Ns, logNs);
+        Ns <<= 4;
+        logNs += 4;
+      }
+    }
+    V* rows = reinterpret_cast<V*>(const_cast<void*>(t.scratch)) + (size_t)sig * B * R1;
+    for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
+      const unsigned w = idx % W, b = idx / W;
+      if (w >= np) continue;
+      const unsigned long long m1 = p0 + w;
+      const V y = cconj(buf[w * a.region + pad16((int)b)]);
+      const unsigned long long e = ((m1 * b) % Mc) * sM;
+      rows[(size_t)b * R1 + m1] = cscale(cmulc(y, tw_global<V>(t.wM, t.wM_lo_n, t.wM_bits, e)), S);
     }
     __syncthreads();
   }

@@ -36,6 +36,13 @@ def run(torch, x, M, code):
     return X, plan
 
 
+def expected_passes(code, N, M):
+    real = code in (adfft.R32, adfft.R64)
+    Nc, Mc = (N // 2, M // 2) if real else (N, M)
+    limit = 8192 if code in (adfft.R64, adfft.C128) else 16384
+    return 2 if np.gcd(Nc, Mc) > limit else 1
+
+
 def sample_bins(M, n, seed):
     rng = np.random.default_rng(seed)
     return np.unique(np.concatenate([np.arange(8), M - 1 - np.arange(8), [M // 2 - 1, M // 2, M // 2 + 1],
@@ -88,3 +95,51 @@ def test_large_real_workload_sampled():
         ref = oracle.alpha_dft(x[s].astype(np.float64), M, bins=bins)
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= tol_for(M, False), err
+
+
+@pytest.mark.parametrize("code,N,alpha", [(adfft.C128, 1 << 14, 2), (adfft.R64, 1 << 15, 2),
+                                          (adfft.C128, 1 << 14, 4)])
+def test_two_pass_adjoint_matches_oracle(code, N, alpha):
+    torch = _torch()
+    M = int(round(alpha * N))
+    real = code == adfft.R64
+    rng = np.random.default_rng(N + 7)
+    g = (rng.standard_normal((1, M)) + 1j * rng.standard_normal((1, M)))
+    dev = torch.device("cuda:0")
+    plan = adfft.Plan(N, batch=1, dtype=code, M=M)
+    assert plan.info.passes == expected_passes(code, N, M) == 2
+    gt = torch.from_numpy(g).to(dev)
+    xb = torch.empty((1, N), dtype=torch.float64 if real else torch.complex128, device=dev)
+    plan.execute_adjoint(gt.data_ptr(), xb.data_ptr())
+    plan.sync_status()
+    ref = oracle.alpha_dft_adjoint(g, N, real_input=real)
+    got = xb.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-12
+
+
+@pytest.mark.parametrize("code,N,alpha", [(adfft.R32, 1 << 17, 8), (adfft.C64, 1 << 15, 3),
+                                          (adfft.R32, 1 << 17, 2.5), (adfft.R32, 1 << 22, 16)])
+def test_two_pass_adjoint_dot_product(code, N, alpha):
+    """<A x, g> = <x, A^H g> through the forward and adjoint two-pass launches."""
+    torch = _torch()
+    M = int(round(alpha * N))
+    real = code == adfft.R32
+    dev = torch.device("cuda:0")
+    gen = torch.Generator(device=dev).manual_seed(5)
+    if real:
+        x = torch.randn((1, N), device=dev, generator=gen)
+    else:
+        x = torch.randn((1, N), device=dev, generator=gen, dtype=torch.complex64)
+    g = torch.randn((1, M), device=dev, generator=gen, dtype=torch.complex64)
+    plan = adfft.Plan(N, batch=1, dtype=code, M=M)
+    assert plan.info.passes == expected_passes(code, N, M)
+    X = torch.empty((1, M), dtype=torch.complex64, device=dev)
+    xb = torch.empty_like(x)
+    plan.execute(x.data_ptr(), X.data_ptr())
+    plan.execute_adjoint(g.data_ptr(), xb.data_ptr())
+    plan.sync_status()
+    lhs = torch.vdot(g.flatten().to(torch.complex128), X.flatten().to(torch.complex128))
+    rhs = torch.vdot(xb.flatten().to(torch.complex128), x.flatten().to(torch.complex128))
+    if real:
+        lhs, rhs = lhs.real, rhs.real
+    assert abs((lhs - rhs).item()) <= 5e-6 * max(1.0, abs(lhs.item())) * np.sqrt(np.log2(M))
