@@ -411,14 +411,16 @@ std::vector<T> flatten(const std::vector<std::complex<double>>& v) {
 
 // Configure the chirp-z path (any N, M); returns ADFFT_OK or why it does not apply.
 int setup_bluestein(Plan& p) {
+  if (p.blu_ok) return ADFFT_OK;
   const int64_t Lmax = p.dbl ? 8192 : 16384;
-  if (p.N > Lmax) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  // chunks of B = L - N + 1 >= N + 1 bins: at most 2M/N + 1 kernel spectra of length L
+  if (2 * p.N > Lmax) return ADFFT_ERR_UNSUPPORTED_SIZE;
   int64_t L = 1;
   while (L < p.N + p.M - 1 && L < Lmax) L <<= 1;
-  while (L < p.N) L <<= 1;
+  while (L < 2 * p.N) L <<= 1;
   const int64_t B = L - p.N + 1;
   const int64_t chunks = (p.M + B - 1) / B;
-  if (chunks > 65535 || p.M >= (int64_t(1) << 31)) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  if (chunks > 4096 || p.M >= (int64_t(1) << 31)) return ADFFT_ERR_UNSUPPORTED_SIZE;
   const int vpt = fused_values_per_thread(p.dbl);
   const size_t esz = p.dbl ? 16 : 8;
   const int bits = (ilog2(L) + 1) / 2;
@@ -626,11 +628,14 @@ adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dty
   }
   const int rc_fold = setup_fold(p);
   if (rc_fold != ADFFT_OK && rc_fold != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_fold, h);
-  const int rc_blu = setup_bluestein(p);
-  if (rc_blu != ADFFT_OK && rc_blu != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_blu, h);
   if (!p.fold_ok) {
     const int rc_tp = setup_twopass(p);
     if (rc_tp != ADFFT_OK && rc_tp != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_tp, h);
+  }
+  // the chirp-z form is set up here only when no fold form applies (else on request)
+  if (!p.fold_ok && !p.tp_ok) {
+    const int rc_blu = setup_bluestein(p);
+    if (rc_blu != ADFFT_OK && rc_blu != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_blu, h);
   }
   if (p.fold_ok || p.tp_ok) p.algo = ADFFT_ALGO_FOLD;
   else if (p.blu_ok) p.algo = ADFFT_ALGO_BLUESTEIN;
@@ -707,7 +712,11 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
     return ADFFT_OK;
   }
   if (algo == ADFFT_ALGO_BLUESTEIN) {
-    if (!p.blu_ok) return ADFFT_ERR_NOT_SUPPORTED;
+    if (!p.blu_ok) {
+      const int rc = adfft::setup_bluestein(p);
+      if (rc == ADFFT_ERR_UNSUPPORTED_SIZE) return ADFFT_ERR_NOT_SUPPORTED;
+      if (rc != ADFFT_OK) return rc;
+    }
     p.algo = algo;
     return ADFFT_OK;
   }
