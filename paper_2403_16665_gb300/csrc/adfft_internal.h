@@ -133,6 +133,14 @@ cudaError_t twopass_prepare(const TwoPassLaunch& L);
 cudaError_t twopass_launch(const TwoPassLaunch& L, const void* scratch, void* out, cudaStream_t stream);
 cudaError_t twopass_adjoint_launch(const TwoPassLaunch& L, const void* g, void* scratch, cudaStream_t stream);
 
+// Tensor-core (precision form) launchers (fused_tc_fp16.cu, fused_tc_bf16.cu).
+cudaError_t tc_prepare_fp16(const FusedLaunch* L, const TwoPassLaunch* L2);
+cudaError_t tc_launch_fused_fp16(const FusedLaunch& L, const void* in, void* out, cudaStream_t s);
+cudaError_t tc_launch_columns_fp16(const TwoPassLaunch& L, const void* scratch, void* out, cudaStream_t s);
+cudaError_t tc_prepare_bf16(const FusedLaunch* L, const TwoPassLaunch* L2);
+cudaError_t tc_launch_fused_bf16(const FusedLaunch& L, const void* in, void* out, cudaStream_t s);
+cudaError_t tc_launch_columns_bf16(const TwoPassLaunch& L, const void* scratch, void* out, cudaStream_t s);
+
 // Chirp-z launchers (bluestein.cu).
 cudaError_t bluestein_prepare(const BluesteinLaunch& L);
 cudaError_t bluestein_launch(const BluesteinLaunch& L, const void* in, void* out, cudaStream_t stream);

@@ -139,14 +139,21 @@ __device__ __forceinline__ void apply_stage_twiddles(V (*v)[R], V w1) {
 // is twiddled by W_Mt^{s r n} = W_Mt^{s r j} * c^i * g^f with the per-residue
 // constants c = W_Mt^{s r Np/R} and g = W_Mt^{s r Np} (s = Mt/Mc), so each
 // (j, r) costs one table lookup.
-template <int R, typename V>
-__device__ __forceinline__ V ld_any(const FusedArgs& a, const void* u, int idx, int mode, bool staged) {
-  if (mode == kColumns) return ld_col<V>(u, idx, a.cols);
-  return ld_u<V>(u, idx, mode, staged);
+template <typename V, bool STAGED>
+__device__ __forceinline__ V ld_any(const FusedArgs& a, const void* u, const V* su, int idx, int mode) {
+  using R = typename real_of<V>::type;
+  if constexpr (STAGED) {
+    // the staged copy in this CTA's shared memory (typed, so it compiles to shared loads)
+    if (mode == kLoadRealPlain) return cmake<V>(reinterpret_cast<const R*>(su)[idx], (R)0);
+    return su[idx];
+  } else {
+    if (mode == kColumns) return ld_col<V>(u, idx, a.cols);
+    return ld_u<V>(u, idx, mode, false);
+  }
 }
 
-template <int R, typename V>
-__device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, int mode, bool staged,
+template <int R, typename V, bool STAGED>
+__device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, const V* su, int mode,
                                            V* buf, const TwTable<V>& tab, int r0) {
   const int items = a.Np / R;
   const unsigned T = blockDim.x;
@@ -163,12 +170,12 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, in
       V acc[R];
       // fold: acc[i] = sum_f u[j + i items + f Np] g^f
 #pragma unroll
-      for (int i = 0; i < R; ++i) acc[i] = ld_any<R, V>(a, u, j + i * items, mode, staged);
+      for (int i = 0; i < R; ++i) acc[i] = ld_any<V, STAGED>(a, u, su, j + i * items, mode);
       if (a.q > 1) {
         V gf = g1;
         for (int f = 1; f < a.q; ++f) {
 #pragma unroll
-          for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_any<R, V>(a, u, j + i * items + f * a.Np, mode, staged), gf));
+          for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_any<V, STAGED>(a, u, su, j + i * items + f * a.Np, mode), gf));
           gf = cmul(gf, g1);
         }
       }
@@ -263,8 +270,20 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
 template <typename V, int MODE>
 constexpr int epilogue_unroll() { return sizeof(V) == 16 ? 4 : (MODE == kLoadRealPacked ? 6 : 8); }
 
+// Radix-16 pass hook: the plain FP32/FP64 pass, or the tensor-core form of
+// tc_dft16.cuh when PREC != 0 (declared here, defined there).
+template <int PREC, int TPT, typename V>
+__device__ void stockham_pass_tc(const FusedArgs& a, V* buf, const TwTable<V>& tab, int Ns, int logNs);
+
+template <int PREC, int VPT, typename V>
+__device__ __forceinline__ void radix16_pass(const FusedArgs& a, V* buf, const TwTable<V>& tab, int Ns, int logNs) {
+  if constexpr (PREC == 0) stockham_pass<16, VPT, V>(a, buf, tab, Ns, logNs);
+  else stockham_pass_tc<PREC, VPT / 8, V>(a, buf, tab, Ns, logNs);
+}
+
 // R0: radix of the first pass (1, 2, 4, 8 or 16); every later pass is radix 16.
-template <typename V, int MODE, int VPT, int R0>
+// PREC: arithmetic of the radix-16 passes (0 native, else the tensor-core form).
+template <typename V, int MODE, int VPT, int R0, int PREC = 0>
 __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   using Rl = typename real_of<V>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -302,15 +321,15 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   const unsigned j_first = c * per;
   const unsigned j_last = min(jtot, j_first + per) - 1;      // inclusive
   const unsigned k_first = j_first / P + threadIdx.x / P;
-  const V* base_u;
-  const V* base_p;
+  // shared::cluster addresses of this lane's two source residue regions
+  uint32_t base_u, base_p;
   {
     const unsigned rp = (P - r_l) % P;                        // residue of the mirror bin Mc - j
     const unsigned ou = r_l / (unsigned)a.RPC, op = rp / (unsigned)a.RPC;
     const V* lu = buf + (r_l - ou * a.RPC) * a.region;
     const V* lp = buf + (rp - op * a.RPC) * a.region;
-    base_u = (a.C > 1) ? cluster.map_shared_rank(lu, ou) : lu;
-    base_p = (a.C > 1) ? cluster.map_shared_rank(lp, op) : lp;
+    base_u = dsmem_addr(lu, (a.C > 1) ? ou : (uint32_t)c);
+    base_p = dsmem_addr(lp, (a.C > 1) ? op : (uint32_t)c);
   }
   const int r0 = c * a.RPC;
   const Rl S = (Rl)a.scale;
@@ -347,7 +366,8 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 
     // ---- K1: fold + residue twiddle + first radix
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
-    first_pass<R0, V>(a, u, MODE, staged, buf, tab, r0);
+    if (staged) first_pass<R0, V, true>(a, u, reinterpret_cast<const V*>(stage), MODE, buf, tab, r0);
+    else first_pass<R0, V, false>(a, u, nullptr, MODE, buf, tab, r0);
     __syncthreads();
 
     // prefetch the next signal's input while this one is transformed
@@ -362,7 +382,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     // ---- K2: radix-16 Stockham passes in shared memory
     int Ns = R0, logNs = LOGR0;
     for (int p = 1; p < a.nrad; ++p) {
-      stockham_pass<16, VPT, V>(a, buf, tab, Ns, logNs);
+      radix16_pass<PREC, VPT, V>(a, buf, tab, Ns, logNs);
       Ns <<= 4;
       logNs += 4;
     }
@@ -381,8 +401,8 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
             const unsigned j = k * P + r_l;
             if (j <= half && j <= j_last) {
               const unsigned kp = (r_l == 0) ? ((unsigned)a.Np - k) & ((unsigned)a.Np - 1) : (unsigned)a.Np - 1 - k;
-              Ua[e] = base_u[pad16((int)k)];
-              Ub[e] = base_p[pad16((int)kp)];
+              Ua[e] = dsmem_ld(base_u + (uint32_t)pad16((int)k) * (uint32_t)sizeof(V), V{});
+              Ub[e] = dsmem_ld(base_p + (uint32_t)pad16((int)kp) * (uint32_t)sizeof(V), V{});
             }
           }
 #pragma unroll
@@ -395,11 +415,11 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
               const V wO = cmul(tab(j), O);
               const V X1 = cscale(cadd(E, wO), S);
               const V X2 = cscale(csub(E, wO), S);
-              out[j] = X1;
-              out[j + Mc] = X2;
+              st_stream(out + j, X1);
+              st_stream(out + j + Mc, X2);
               if (j != 0 && 2 * j != Mc) {
-                out[Mc - j] = cconj(X2);
-                out[(unsigned long long)a.M - j] = cconj(X1);
+                st_stream(out + (Mc - j), cconj(X2));
+                st_stream(out + ((unsigned long long)a.M - j), cconj(X1));
               }
             }
           }
@@ -410,7 +430,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 #pragma unroll
           for (int e = 0; e < kEpilogueUnroll; ++e) {
             const unsigned k = kb + e * k_step;
-            if (k * P + r_l <= j_last) Ua[e] = base_u[pad16((int)k)];
+            if (k * P + r_l <= j_last) Ua[e] = dsmem_ld(base_u + (uint32_t)pad16((int)k) * (uint32_t)sizeof(V), V{});
           }
 #pragma unroll
           for (int e = 0; e < kEpilogueUnroll; ++e) {
@@ -425,7 +445,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
                 const V* hi = lo + a.post_lo_n;
                 y = cmul(y, cmul(__ldg(hi + (e2 >> a.post_bits)), __ldg(lo + (e2 & ((1ull << a.post_bits) - 1)))));
               }
-              out[m] = y;
+              st_stream(out + m, y);
             }
           }
         }

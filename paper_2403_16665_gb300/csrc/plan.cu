@@ -507,13 +507,19 @@ int cuda_status_of(cudaError_t e) { return cuda_status(e); }
 
 int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s) {
   cudaError_t e;
+  const bool tc = p.precision != ADFFT_PREC_NATIVE;
+  const bool f16 = p.precision == ADFFT_PREC_FP16X2;
   if (p.algo == ADFFT_ALGO_BLUESTEIN) {
     e = bluestein_launch(p.blu, in, out, s);
   } else if (p.fold_ok) {
-    e = fused_launch(p.fused, in, out, s);
+    e = !tc ? fused_launch(p.fused, in, out, s)
+            : f16 ? tc_launch_fused_fp16(p.fused, in, out, s) : tc_launch_fused_bf16(p.fused, in, out, s);
   } else {
-    e = fused_launch(p.tp1, in, p.d_ws, s);
-    if (e == cudaSuccess) e = twopass_launch(p.tp2, p.d_ws, out, s);
+    e = !tc ? fused_launch(p.tp1, in, p.d_ws, s)
+            : f16 ? tc_launch_fused_fp16(p.tp1, in, p.d_ws, s) : tc_launch_fused_bf16(p.tp1, in, p.d_ws, s);
+    if (e == cudaSuccess)
+      e = !tc ? twopass_launch(p.tp2, p.d_ws, out, s)
+              : f16 ? tc_launch_columns_fp16(p.tp2, p.d_ws, out, s) : tc_launch_columns_bf16(p.tp2, p.d_ws, out, s);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -724,13 +730,25 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
 }
 
 int adfft_plan_set_precision(adfft_plan_t plan, int mode) {
+  using namespace adfft;
   if (!plan) return ADFFT_ERR_INVALID_ARG;
+  Plan& p = plan->p;
   if (mode == ADFFT_PREC_NATIVE) {
-    plan->p.precision = mode;
+    p.precision = mode;
     return ADFFT_OK;
   }
-  if (mode == ADFFT_PREC_FP16X2 || mode == ADFFT_PREC_BF16X3) return ADFFT_ERR_NOT_SUPPORTED;
-  return ADFFT_ERR_INVALID_ARG;
+  if (mode != ADFFT_PREC_FP16X2 && mode != ADFFT_PREC_BF16X3) return ADFFT_ERR_INVALID_ARG;
+  // tensor-core radix-16 passes: complex64 data in the fold forms (not chirp-z, not ragged)
+  if (p.dbl || p.ragged || (!p.fold_ok && !p.tp_ok)) return ADFFT_ERR_NOT_SUPPORTED;
+  const FusedLaunch* L1 = p.fold_ok ? &p.fused : &p.tp1;
+  const TwoPassLaunch* L2 = p.fold_ok ? nullptr : &p.tp2;
+  cudaError_t e = (mode == ADFFT_PREC_FP16X2) ? tc_prepare_fp16(L1, L2) : tc_prepare_bf16(L1, L2);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  p.precision = mode;
+  return ADFFT_OK;
 }
 
 int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {

@@ -40,7 +40,7 @@ __device__ __forceinline__ V tw_global(const void* t, int lo_n, int bits, unsign
   return cmul(__ldg(hi + (e >> bits)), __ldg(lo + (e & ((1ull << bits) - 1))));
 }
 
-template <typename V, int VPT, int R0>
+template <typename V, int VPT, int R0, int PREC = 0>
 __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs t) {
   using Rl = typename real_of<V>::type;
   const FusedArgs& a = t.f;
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
         logNs = LOGR0;
       }
       for (int p = 1; p < a.nrad; ++p) {
-        stockham_pass<16, VPT, V>(a, buf, tab, Ns, logNs);
+        radix16_pass<PREC, VPT, V>(a, buf, tab, Ns, logNs);
         Ns <<= 4;
         logNs += 4;
       }
