@@ -11,6 +11,9 @@ using KernelFn = void (*)(const FusedArgs);
 template <typename V, int MODE, int VPT>
 KernelFn pick_r0(int r0) {
   switch (r0) {
+    case 32:
+      if constexpr (VPT >= 32) return adjoint_kernel<V, MODE, VPT, 32>;
+      else return nullptr;
     case 1: return adjoint_kernel<V, MODE, VPT, 1>;
     case 2: return adjoint_kernel<V, MODE, VPT, 2>;
     case 4: return adjoint_kernel<V, MODE, VPT, 4>;

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
   const unsigned Mt = (unsigned)a.Mt;
   const unsigned s = Mt / Mc;
   const Rl S = (Rl)a.scale;
-  constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : 4;
+  constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : R0 == 16 ? 4 : 5;
   constexpr int UNR = 4;
 
   // this CTA's range of output samples n of the complex core

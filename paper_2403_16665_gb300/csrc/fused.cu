@@ -13,6 +13,9 @@ using KernelFn = void (*)(const FusedArgs);
 template <typename V, int MODE, int VPT>
 KernelFn pick_r0(int r0) {
   switch (r0) {
+    case 32:
+      if constexpr (VPT >= 32) return fused_forward_kernel<V, MODE, VPT, 32>;
+      else return nullptr;
     case 1: return fused_forward_kernel<V, MODE, VPT, 1>;
     case 2: return fused_forward_kernel<V, MODE, VPT, 2>;
     case 4: return fused_forward_kernel<V, MODE, VPT, 4>;
@@ -21,7 +24,14 @@ KernelFn pick_r0(int r0) {
   }
 }
 
+// Shapes with a compile-time specialisation (all strides and pass counts constant).
+using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2>;   // real fp32, packed sub-FFT 8192, 8 residues, 2 per CTA
+
 KernelFn pick_kernel(const FusedLaunch& L) {
+  const FusedArgs& a = L.args;
+  if (!L.dbl && L.mode == kLoadRealPacked && L.r0 == 32 && a.logNp == 13 && a.RPC == 2 && a.P == 8 &&
+      L.threads == 512 && a.Mt == 2 * a.Mc)
+    return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8>;
   if (L.dbl) {
     switch (L.mode) {
       case kLoadComplex: return pick_r0<double2, kLoadComplex, kVptF64>(L.r0);

@@ -72,6 +72,46 @@ struct FusedArgs {
   long long Mpost;
 };
 
+// Compile-time shape of a specialised instantiation; a zero field is read from
+// FusedArgs at run time instead.  LOGNP: log2 of the sub-FFT length, RPC:
+// residues per CTA, P: residues per signal, T: threads per CTA, MTF: Mt / (P Np)
+// (2 for packed real input, 1 otherwise).
+template <int LOGNP = 0, int RPC = 0, int P = 0, int T = 0, int MTF = 0>
+struct Shape {
+  static constexpr bool fixed = LOGNP != 0 && RPC != 0 && P != 0 && T != 0 && MTF != 0;
+  __device__ static __forceinline__ int logNp(const struct FusedArgs& a);
+  __device__ static __forceinline__ int Np(const struct FusedArgs& a);
+  __device__ static __forceinline__ int rpc(const struct FusedArgs& a);
+  __device__ static __forceinline__ int p(const struct FusedArgs& a);
+  __device__ static __forceinline__ int threads();
+  __device__ static __forceinline__ int region(const struct FusedArgs& a);
+  __device__ static __forceinline__ unsigned mt(const struct FusedArgs& a);
+};
+template <int L, int R, int PP, int TT, int F>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F>::logNp(const FusedArgs& a) { return L ? L : a.logNp; }
+template <int L, int R, int PP, int TT, int F>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F>::Np(const FusedArgs& a) { return L ? (1 << L) : a.Np; }
+template <int L, int R, int PP, int TT, int F>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F>::rpc(const FusedArgs& a) { return R ? R : a.RPC; }
+template <int L, int R, int PP, int TT, int F>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F>::p(const FusedArgs& a) { return PP ? PP : a.P; }
+template <int L, int R, int PP, int TT, int F>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F>::threads() { return TT ? TT : (int)blockDim.x; }
+template <int L, int R, int PP, int TT, int F>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F>::region(const FusedArgs& a) {
+  return L ? ((1 << L) + (1 << L) / 16 + 2) : a.region;
+}
+template <int L, int R, int PP, int TT, int F>
+__device__ __forceinline__ unsigned Shape<L, R, PP, TT, F>::mt(const FusedArgs& a) {
+  return (L && PP && F) ? (unsigned)(F * PP) << L : (unsigned)a.Mt;
+}
+using RuntimeShape = Shape<>;
+
+// Passes of a fixed shape: one of radix 2^LOGR0, then radix 16.
+template <class SH, int LOGR0> struct SH_PASSES;
+template <int L, int R, int PP, int TT, int F, int LOGR0>
+struct SH_PASSES<Shape<L, R, PP, TT, F>, LOGR0> { static constexpr int value = 1 + (L - LOGR0) / 4; };
+
 // Shared-memory layout of the fused kernel (byte offsets).
 struct FusedSmem {
   int tw, stage, buf, total;
@@ -152,20 +192,24 @@ __device__ __forceinline__ V ld_any(const FusedArgs& a, const void* u, const V* 
   }
 }
 
-template <int R, typename V, bool STAGED>
+template <int R, typename V, bool STAGED, class SH = RuntimeShape>
 __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, const V* su, int mode,
                                            V* buf, const TwTable<V>& tab, int r0) {
-  const int items = a.Np / R;
-  const unsigned T = blockDim.x;
-  const unsigned Mt = (unsigned)a.Mt;
-  const unsigned s = (unsigned)(a.Mt / a.Mc);
-  for (int rl = 0; rl < a.RPC; ++rl) {
+  const int Np = SH::Np(a);
+  const int items = Np / R;
+  const unsigned T = (unsigned)SH::threads();
+  const unsigned Mt = SH::mt(a);
+  const unsigned s = SH::fixed ? Mt / ((unsigned)SH::p(a) << SH::logNp(a)) : (unsigned)(a.Mt / a.Mc);
+  const int rpc = SH::rpc(a);
+  const int region = SH::region(a);
+#pragma unroll 1
+  for (int rl = 0; rl < rpc; ++rl) {
     const unsigned long long sr = (unsigned long long)s * (unsigned)(r0 + rl);
     const V c1 = tab((unsigned)((sr * (unsigned)items) % Mt));
-    const V g1 = tab((unsigned)((sr * (unsigned)a.Np) % Mt));
+    const V g1 = tab((unsigned)((sr * (unsigned)Np) % Mt));
     const unsigned d_T = (unsigned)((sr * T) % Mt);
     unsigned e_j = (unsigned)((sr * threadIdx.x) % Mt);
-    V* dst = buf + rl * a.region;
+    V* dst = buf + rl * region;
     for (int j = threadIdx.x; j < items; j += T) {
       V acc[R];
       // fold: acc[i] = sum_f u[j + i items + f Np] g^f
@@ -175,7 +219,7 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, co
         V gf = g1;
         for (int f = 1; f < a.q; ++f) {
 #pragma unroll
-          for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_any<V, STAGED>(a, u, su, j + i * items + f * a.Np, mode), gf));
+          for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_any<V, STAGED>(a, u, su, j + i * items + f * Np, mode), gf));
           gf = cmul(gf, g1);
         }
       }
@@ -201,17 +245,18 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, co
 // runs DFT_R and writes to (j / Ns) * Ns * R + (j mod Ns) + i*Ns.  When the
 // block size is a multiple of Np/R every item of a thread has the same j, and
 // the twiddles are computed once for all of its residues.
-template <int R, int VPT, typename V>
+template <int R, int VPT, typename V, class SH = RuntimeShape>
 __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const TwTable<V>& tab,
                                               int Ns, int logNs) {
   constexpr int IPT = VPT / R;
   constexpr int LOGR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
-  const int log_items = a.logNp - LOGR;
+  const int log_items = SH::logNp(a) - LOGR;
   const int items_res = 1 << log_items;
-  const int items = a.RPC * items_res;
-  const int T = blockDim.x;
+  const int items = SH::rpc(a) * items_res;
+  const int T = SH::threads();
+  const int region = SH::region(a);
   const bool same_j = (T & (items_res - 1)) == 0;
-  const unsigned tw_step = (unsigned)a.Mt / ((unsigned)Ns << LOGR);   // Mt / (Ns R)
+  const unsigned tw_step = SH::mt(a) / ((unsigned)Ns << LOGR);   // Mt / (Ns R)
   // pad16(j + i*S) = pad16(j) + i*(S + S/16) for S a multiple of 16
   const int in_step = items_res + (items_res >> 4);
   V v[IPT][R];
@@ -220,7 +265,7 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
     const int wi = threadIdx.x + it * T;
     const int rl = wi >> log_items;
     const int j = wi & (items_res - 1);
-    const V* src = buf + rl * a.region;
+    const V* src = buf + rl * region;
     if (items_res >= 16) {
       const V* p0 = src + pad16(j);
 #pragma unroll
@@ -252,7 +297,7 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
       const int j = wi & (items_res - 1);
       const int k = j & (Ns - 1);
       const int base = ((j >> logNs) << (logNs + LOGR)) + k;
-      V* dst = buf + rl * a.region;
+      V* dst = buf + rl * region;
       if (Ns >= 16) {
         V* p0 = dst + pad16(base);
 #pragma unroll
@@ -275,21 +320,21 @@ constexpr int epilogue_unroll() { return sizeof(V) == 16 ? 4 : (MODE == kLoadRea
 template <int PREC, int TPT, typename V>
 __device__ void stockham_pass_tc(const FusedArgs& a, V* buf, const TwTable<V>& tab, int Ns, int logNs);
 
-template <int PREC, int VPT, typename V>
+template <int PREC, int VPT, typename V, class SH = RuntimeShape>
 __device__ __forceinline__ void radix16_pass(const FusedArgs& a, V* buf, const TwTable<V>& tab, int Ns, int logNs) {
-  if constexpr (PREC == 0) stockham_pass<16, VPT, V>(a, buf, tab, Ns, logNs);
+  if constexpr (PREC == 0) stockham_pass<16, VPT, V, SH>(a, buf, tab, Ns, logNs);
   else stockham_pass_tc<PREC, VPT / 8, V>(a, buf, tab, Ns, logNs);
 }
 
 // R0: radix of the first pass (1, 2, 4, 8 or 16); every later pass is radix 16.
 // PREC: arithmetic of the radix-16 passes (0 native, else the tensor-core form).
-template <typename V, int MODE, int VPT, int R0, int PREC = 0>
+template <typename V, int MODE, int VPT, int R0, int PREC = 0, class SH = RuntimeShape>
 __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   using Rl = typename real_of<V>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int esz = (int)sizeof(V);
   const int tw_n = a.tw_lo_n + a.tw_hi_n;
-  const FusedSmem L = fused_smem_layout(tw_n, a.stage_bytes, a.RPC, a.region, esz);
+  const FusedSmem L = fused_smem_layout(tw_n, a.stage_bytes, SH::rpc(a), SH::region(a), esz);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   V* tw_s = reinterpret_cast<V*>(smem_raw + L.tw);
   unsigned char* stage = smem_raw + L.stage;
@@ -311,8 +356,9 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   // input: j <= Mc/2 and their mirrors), per a multiple of P.  Thread t keeps the
   // residue r_l = t mod P for every j it handles (T' = P * floor(T/P) threads
   // take part), so its shared-memory sources are fixed for the whole kernel.
-  const unsigned P = (unsigned)a.P;
-  const unsigned Tp = (blockDim.x / P) * P;
+  const unsigned P = (unsigned)SH::p(a);
+  const unsigned RPCu = (unsigned)SH::rpc(a);
+  const unsigned Tp = ((unsigned)SH::threads() / P) * P;
   const bool lane_ok = threadIdx.x < Tp;
   const unsigned r_l = threadIdx.x % P;
   const unsigned k_step = Tp / P;
@@ -325,15 +371,15 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   uint32_t base_u, base_p;
   {
     const unsigned rp = (P - r_l) % P;                        // residue of the mirror bin Mc - j
-    const unsigned ou = r_l / (unsigned)a.RPC, op = rp / (unsigned)a.RPC;
-    const V* lu = buf + (r_l - ou * a.RPC) * a.region;
-    const V* lp = buf + (rp - op * a.RPC) * a.region;
+    const unsigned ou = r_l / RPCu, op = rp / RPCu;
+    const V* lu = buf + (r_l - ou * RPCu) * SH::region(a);
+    const V* lp = buf + (rp - op * RPCu) * SH::region(a);
     base_u = dsmem_addr(lu, (a.C > 1) ? ou : (uint32_t)c);
     base_p = dsmem_addr(lp, (a.C > 1) ? op : (uint32_t)c);
   }
-  const int r0 = c * a.RPC;
+  const int r0 = c * SH::rpc(a);
   const Rl S = (Rl)a.scale;
-  constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : 4;
+  constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : R0 == 16 ? 4 : 5;
   constexpr int kEpilogueUnroll = epilogue_unroll<V, MODE>();
   uint32_t phase = 0, fail_phase = 0;
   bool failed = false;
@@ -366,8 +412,8 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 
     // ---- K1: fold + residue twiddle + first radix
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
-    if (staged) first_pass<R0, V, true>(a, u, reinterpret_cast<const V*>(stage), MODE, buf, tab, r0);
-    else first_pass<R0, V, false>(a, u, nullptr, MODE, buf, tab, r0);
+    if (staged) first_pass<R0, V, true, SH>(a, u, reinterpret_cast<const V*>(stage), MODE, buf, tab, r0);
+    else first_pass<R0, V, false, SH>(a, u, nullptr, MODE, buf, tab, r0);
     __syncthreads();
 
     // prefetch the next signal's input while this one is transformed
@@ -381,10 +427,20 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 
     // ---- K2: radix-16 Stockham passes in shared memory
     int Ns = R0, logNs = LOGR0;
-    for (int p = 1; p < a.nrad; ++p) {
-      radix16_pass<PREC, VPT, V>(a, buf, tab, Ns, logNs);
-      Ns <<= 4;
-      logNs += 4;
+    if constexpr (SH::fixed) {
+      constexpr int kPasses = SH_PASSES<SH, LOGR0>::value;
+#pragma unroll
+      for (int p = 1; p < kPasses; ++p) {
+        radix16_pass<PREC, VPT, V, SH>(a, buf, tab, Ns, logNs);
+        Ns <<= 4;
+        logNs += 4;
+      }
+    } else {
+      for (int p = 1; p < a.nrad; ++p) {
+        radix16_pass<PREC, VPT, V, SH>(a, buf, tab, Ns, logNs);
+        Ns <<= 4;
+        logNs += 4;
+      }
     }
 
     // ---- K3: interleave epilogue through distributed shared memory
@@ -400,7 +456,8 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
             const unsigned k = kb + e * k_step;
             const unsigned j = k * P + r_l;
             if (j <= half && j <= j_last) {
-              const unsigned kp = (r_l == 0) ? ((unsigned)a.Np - k) & ((unsigned)a.Np - 1) : (unsigned)a.Np - 1 - k;
+              const unsigned Npu = (unsigned)SH::Np(a);
+              const unsigned kp = (r_l == 0) ? (Npu - k) & (Npu - 1) : Npu - 1 - k;
               Ua[e] = dsmem_ld(base_u + (uint32_t)pad16((int)k) * (uint32_t)sizeof(V), V{});
               Ub[e] = dsmem_ld(base_p + (uint32_t)pad16((int)kp) * (uint32_t)sizeof(V), V{});
             }

@@ -140,9 +140,11 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   a.status = status;
   a.cols = 1;
   a.in_unit = (mode == kLoadComplex || mode == kColumns) ? (int)esz : (int)(esz / 2);
-  // passes: a first pass of radix R0 = 2^(log2 Np mod 4) (16 if that is 0), then radix 16
+  // passes: a first pass of radix R0 = 2^(log2 Np mod 4) (16 if that is 0), then radix 16;
+  // for complex64 data a remainder of 2 is merged with one radix-16 pass into radix 32
   const int L2 = a.logNp;
   int lr0 = (L2 == 0) ? 0 : (L2 % 4 ? L2 % 4 : 4);
+  if (!dbl && lr0 == 1 && L2 >= 5) lr0 = 5;
   a.nrad = 1 + (L2 - lr0) / 4;
   L.r0 = 1 << lr0;
   a.divP = make_fastdiv((uint32_t)P);

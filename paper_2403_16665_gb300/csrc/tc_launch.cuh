@@ -16,6 +16,7 @@ struct TcKernels {
   template <int MODE>
   static FusedFn fused_r0(int r0) {
     switch (r0) {
+      case 32: return fused_forward_kernel<float2, MODE, 32, 32, PREC>;
       case 1: return fused_forward_kernel<float2, MODE, 32, 1, PREC>;
       case 2: return fused_forward_kernel<float2, MODE, 32, 2, PREC>;
       case 4: return fused_forward_kernel<float2, MODE, 32, 4, PREC>;
