@@ -25,7 +25,9 @@ KernelFn pick_r0(int r0) {
 }
 
 // Shapes with a compile-time specialisation (all strides and pass counts constant).
-using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2>;   // real fp32, packed sub-FFT 8192, 8 residues, 2 per CTA
+// real fp32, packed sub-FFT 8192, 8 residues, 2 per CTA, 512 threads; pad 1 per 32 (radix-32 first
+// pass writes at stride 32 without bank conflicts); 6 epilogue loads in flight per thread
+using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2, 5, 6>;
 
 KernelFn pick_kernel(const FusedLaunch& L) {
   const FusedArgs& a = L.args;

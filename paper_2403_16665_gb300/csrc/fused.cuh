@@ -76,9 +76,14 @@ struct FusedArgs {
 // FusedArgs at run time instead.  LOGNP: log2 of the sub-FFT length, RPC:
 // residues per CTA, P: residues per signal, T: threads per CTA, MTF: Mt / (P Np)
 // (2 for packed real input, 1 otherwise).
-template <int LOGNP = 0, int RPC = 0, int P = 0, int T = 0, int MTF = 0>
+// PADSH: shared-memory padding of one slot per 2^PADSH elements (0: 4, i.e. pad16);
+// EU: independent epilogue loads in flight per thread (0: the generic default).
+template <int LOGNP = 0, int RPC = 0, int P = 0, int T = 0, int MTF = 0, int PADSH = 0, int EU = 0>
 struct Shape {
   static constexpr bool fixed = LOGNP != 0 && RPC != 0 && P != 0 && T != 0 && MTF != 0;
+  static constexpr int padsh = PADSH ? PADSH : 4;
+  static constexpr int eu = EU;
+  __device__ static __forceinline__ int pad(int p) { return p + (p >> padsh); }
   __device__ static __forceinline__ int logNp(const struct FusedArgs& a);
   __device__ static __forceinline__ int Np(const struct FusedArgs& a);
   __device__ static __forceinline__ int rpc(const struct FusedArgs& a);
@@ -87,30 +92,30 @@ struct Shape {
   __device__ static __forceinline__ int region(const struct FusedArgs& a);
   __device__ static __forceinline__ unsigned mt(const struct FusedArgs& a);
 };
-template <int L, int R, int PP, int TT, int F>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F>::logNp(const FusedArgs& a) { return L ? L : a.logNp; }
-template <int L, int R, int PP, int TT, int F>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F>::Np(const FusedArgs& a) { return L ? (1 << L) : a.Np; }
-template <int L, int R, int PP, int TT, int F>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F>::rpc(const FusedArgs& a) { return R ? R : a.RPC; }
-template <int L, int R, int PP, int TT, int F>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F>::p(const FusedArgs& a) { return PP ? PP : a.P; }
-template <int L, int R, int PP, int TT, int F>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F>::threads() { return TT ? TT : (int)blockDim.x; }
-template <int L, int R, int PP, int TT, int F>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F>::region(const FusedArgs& a) {
-  return L ? ((1 << L) + (1 << L) / 16 + 2) : a.region;
+template <int L, int R, int PP, int TT, int F, int PS, int E>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::logNp(const FusedArgs& a) { return L ? L : a.logNp; }
+template <int L, int R, int PP, int TT, int F, int PS, int E>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::Np(const FusedArgs& a) { return L ? (1 << L) : a.Np; }
+template <int L, int R, int PP, int TT, int F, int PS, int E>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::rpc(const FusedArgs& a) { return R ? R : a.RPC; }
+template <int L, int R, int PP, int TT, int F, int PS, int E>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::p(const FusedArgs& a) { return PP ? PP : a.P; }
+template <int L, int R, int PP, int TT, int F, int PS, int E>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::threads() { return TT ? TT : (int)blockDim.x; }
+template <int L, int R, int PP, int TT, int F, int PS, int E>
+__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::region(const FusedArgs& a) {
+  return L ? ((1 << L) + ((1 << L) >> (PS ? PS : 4)) + 2) : a.region;
 }
-template <int L, int R, int PP, int TT, int F>
-__device__ __forceinline__ unsigned Shape<L, R, PP, TT, F>::mt(const FusedArgs& a) {
+template <int L, int R, int PP, int TT, int F, int PS, int E>
+__device__ __forceinline__ unsigned Shape<L, R, PP, TT, F, PS, E>::mt(const FusedArgs& a) {
   return (L && PP && F) ? (unsigned)(F * PP) << L : (unsigned)a.Mt;
 }
 using RuntimeShape = Shape<>;
 
 // Passes of a fixed shape: one of radix 2^LOGR0, then radix 16.
 template <class SH, int LOGR0> struct SH_PASSES;
-template <int L, int R, int PP, int TT, int F, int LOGR0>
-struct SH_PASSES<Shape<L, R, PP, TT, F>, LOGR0> { static constexpr int value = 1 + (L - LOGR0) / 4; };
+template <int L, int R, int PP, int TT, int F, int PS, int E, int LOGR0>
+struct SH_PASSES<Shape<L, R, PP, TT, F, PS, E>, LOGR0> { static constexpr int value = 1 + (L - LOGR0) / 4; };
 
 // Shared-memory layout of the fused kernel (byte offsets).
 struct FusedSmem {
@@ -233,7 +238,7 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, co
       }
       DFT<R, V>::run(acc);
 #pragma unroll
-      for (int i = 0; i < R; ++i) dst[pad16(j * R + i)] = acc[i];
+      for (int i = 0; i < R; ++i) dst[SH::pad(j * R + i)] = acc[i];
       e_j += d_T;
       if (e_j >= Mt) e_j -= Mt;
     }
@@ -257,8 +262,9 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
   const int region = SH::region(a);
   const bool same_j = (T & (items_res - 1)) == 0;
   const unsigned tw_step = SH::mt(a) / ((unsigned)Ns << LOGR);   // Mt / (Ns R)
-  // pad16(j + i*S) = pad16(j) + i*(S + S/16) for S a multiple of 16
-  const int in_step = items_res + (items_res >> 4);
+  // pad(j + i*S) = pad(j) + i*(S + S/2^padsh) for S a multiple of 2^padsh
+  constexpr int PADN = 1 << SH::padsh;
+  const int in_step = items_res + (items_res >> SH::padsh);
   V v[IPT][R];
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
@@ -266,13 +272,13 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
     const int rl = wi >> log_items;
     const int j = wi & (items_res - 1);
     const V* src = buf + rl * region;
-    if (items_res >= 16) {
-      const V* p0 = src + pad16(j);
+    if (items_res >= PADN) {
+      const V* p0 = src + SH::pad(j);
 #pragma unroll
       for (int i = 0; i < R; ++i) v[it][i] = (wi < items) ? p0[i * in_step] : czero<V>();
     } else {
 #pragma unroll
-      for (int i = 0; i < R; ++i) v[it][i] = (wi < items) ? src[pad16(j + (i << log_items))] : czero<V>();
+      for (int i = 0; i < R; ++i) v[it][i] = (wi < items) ? src[SH::pad(j + (i << log_items))] : czero<V>();
     }
   }
   if (same_j) {
@@ -288,7 +294,7 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
 #pragma unroll
   for (int it = 0; it < IPT; ++it) DFT<R, V>::run(v[it]);
   __syncthreads();
-  const int out_step = Ns + (Ns >> 4);
+  const int out_step = Ns + (Ns >> SH::padsh);
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
     const int wi = threadIdx.x + it * T;
@@ -298,13 +304,13 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
       const int k = j & (Ns - 1);
       const int base = ((j >> logNs) << (logNs + LOGR)) + k;
       V* dst = buf + rl * region;
-      if (Ns >= 16) {
-        V* p0 = dst + pad16(base);
+      if (Ns >= PADN) {
+        V* p0 = dst + SH::pad(base);
 #pragma unroll
         for (int i = 0; i < R; ++i) p0[i * out_step] = v[it][i];
       } else {
 #pragma unroll
-        for (int i = 0; i < R; ++i) dst[pad16(base + i * Ns)] = v[it][i];
+        for (int i = 0; i < R; ++i) dst[SH::pad(base + i * Ns)] = v[it][i];
       }
     }
   }
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   const int r0 = c * SH::rpc(a);
   const Rl S = (Rl)a.scale;
   constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : R0 == 16 ? 4 : 5;
-  constexpr int kEpilogueUnroll = epilogue_unroll<V, MODE>();
+  constexpr int kEpilogueUnroll = SH::eu ? SH::eu : epilogue_unroll<V, MODE>();
   uint32_t phase = 0, fail_phase = 0;
   bool failed = false;
 
@@ -458,8 +464,8 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
             if (j <= half && j <= j_last) {
               const unsigned Npu = (unsigned)SH::Np(a);
               const unsigned kp = (r_l == 0) ? (Npu - k) & (Npu - 1) : Npu - 1 - k;
-              Ua[e] = dsmem_ld(base_u + (uint32_t)pad16((int)k) * (uint32_t)sizeof(V), V{});
-              Ub[e] = dsmem_ld(base_p + (uint32_t)pad16((int)kp) * (uint32_t)sizeof(V), V{});
+              Ua[e] = dsmem_ld(base_u + (uint32_t)SH::pad((int)k) * (uint32_t)sizeof(V), V{});
+              Ub[e] = dsmem_ld(base_p + (uint32_t)SH::pad((int)kp) * (uint32_t)sizeof(V), V{});
             }
           }
 #pragma unroll
@@ -487,7 +493,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 #pragma unroll
           for (int e = 0; e < kEpilogueUnroll; ++e) {
             const unsigned k = kb + e * k_step;
-            if (k * P + r_l <= j_last) Ua[e] = dsmem_ld(base_u + (uint32_t)pad16((int)k) * (uint32_t)sizeof(V), V{});
+            if (k * P + r_l <= j_last) Ua[e] = dsmem_ld(base_u + (uint32_t)SH::pad((int)k) * (uint32_t)sizeof(V), V{});
           }
 #pragma unroll
           for (int e = 0; e < kEpilogueUnroll; ++e) {
