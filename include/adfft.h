@@ -74,9 +74,12 @@ typedef enum {
 
 /* Algorithm choice (adfft_plan_set_algorithm). */
 typedef enum {
-    ADFFT_ALGO_AUTO = 0,       /* fold+FFT when g = gcd(M,N) is a power of two and q is small, else chirp-z */
-    ADFFT_ALGO_FOLD = 1,       /* P twiddled length-g FFTs (integer alpha: q = 1) */
-    ADFFT_ALGO_BLUESTEIN = 2   /* chirp-z: mn = (m^2 + n^2 - (m-n)^2)/2, convolution by FFT */
+    ADFFT_ALGO_AUTO = 0,       /* the plan's own choice: the default rule below, or the autotuner's */
+    ADFFT_ALGO_FOLD = 1,       /* P twiddled length-g FFTs in one fused pass (integer alpha: q = 1);
+                                  where no single-pass shape fits, its two-pass variant */
+    ADFFT_ALGO_BLUESTEIN = 2,  /* chirp-z: mn = (m^2 + n^2 - (m-n)^2)/2, convolution by FFT */
+    ADFFT_ALGO_FOUR_STEP = 3   /* the fold form with each length-g FFT split g = A*B over two
+                                  HBM passes (power-of-two g; plan workspace of batch*M complex) */
 } adfft_algo_t;
 
 /* Arithmetic form of the length-g FFT stages (adfft_plan_set_precision). */
@@ -99,6 +102,9 @@ typedef struct {
     int32_t cluster;      /* CTAs per signal sharing one thread-block cluster */
     int32_t passes;       /* HBM passes per forward transform (1 = fused single pass) */
     double scale;         /* S */
+    int32_t staged;       /* 1 if the fused pass stages each signal through shared memory */
+    int32_t tuned;        /* 1 if the launch shape came from the autotuner or its cache
+                             (ragged plans: every shape class) */
 } adfft_plan_info_t;
 
 /*
@@ -175,7 +181,8 @@ int adfft_execute_adjoint(adfft_plan_t plan, const void *d_grad_out, void *d_gra
                           void *stream);
 
 /*
- * Synchronise `stream`, then read and clear the plan's device status word.
+ * Synchronise `stream`, then read and clear the plan's device status word
+ * (a ragged plan: the status word of every shape class).
  * Returns ADFFT_OK, or ADFFT_ERR_TIMEOUT if a kernel of the plan gave up a
  * bounded device-side wait (for example on an asynchronous copy) since the
  * last call; the outputs of the launches concerned are then invalid.  Kernels
@@ -193,6 +200,48 @@ int adfft_plan_sync_status(adfft_plan_t plan, void *stream);
  * plan's status word checked as by adfft_plan_sync_status.
  */
 int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *stream);
+
+/*
+ * Autotuner.  The default rule picks, for the fold form, the longest
+ * power-of-two sub-FFT g' dividing gcd(M, N) (halved for real input) whose
+ * P' = M/g' residues fit one cluster's shared memory, with a fold of at most
+ * 16 blocks (the fold identity holds for every divisor of the gcd), the
+ * smallest such cluster, and input staging where it fits; the two-pass form
+ * only where no single-pass shape fits.
+ *
+ * adfft_plan_autotune times the forward transform of the plan for every
+ * candidate launch shape (sub-FFT length, cluster size, input staging; the
+ * two-pass form where it applies) with `iters` timed launches each (1..100;
+ * 0 means 3) on the caller's buffers, keeps the fastest, and records it in
+ * the process-wide tuning cache under (GPU name, driver version, N, M, batch,
+ * dtype, precision).  d_in and d_out are as for adfft_execute (d_out is
+ * overwritten); for a ragged plan the packed buffers, and every shape class
+ * is tuned.  The call synchronises `stream` and must not run while the stream
+ * is being captured.  Returns ADFFT_OK, or the first error of a launch.
+ *
+ * Plans created later with the same sizes on the same GPU model and driver
+ * take the cached shape; entries of another GPU or driver are kept but never
+ * used.  adfft_autotune_save writes the cache to a JSON file, and
+ * adfft_autotune_load merges a file written by it (ADFFT_ERR_INVALID_ARG for
+ * a file it cannot read or parse; nothing is merged then).
+ * adfft_autotune_clear empties the cache.  The cache is guarded by a mutex;
+ * a plan itself is not thread-safe.
+ */
+int adfft_plan_autotune(adfft_plan_t plan, const void *d_in, void *d_out, void *stream, int iters);
+
+/*
+ * Set the fold form's launch shape by hand (the autotuner's candidates):
+ * fft_len = the sub-FFT length g' (a power of two dividing M and N, halved for
+ * real input; 0 = the largest such), cluster = CTAs per signal (0 = the
+ * smallest that fits), staged = 1 to stage each signal through shared memory,
+ * 0 not to, -1 where it fits.  Selects the fold algorithm.  Returns
+ * ADFFT_ERR_NOT_SUPPORTED (the plan unchanged) when the shape does not fit
+ * one cluster or the plan has no fold form (ragged, or chirp-z only sizes).
+ */
+int adfft_plan_set_launch_shape(adfft_plan_t plan, int64_t fft_len, int cluster, int staged);
+int adfft_autotune_save(const char *path);
+int adfft_autotune_load(const char *path);
+int adfft_autotune_clear(void);
 
 /*
  * Forward transform that allocates no device memory.

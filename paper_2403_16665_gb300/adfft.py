@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libadfft.so")
 # adfft_dtype_t
 R32, C64, R64, C128 = 0, 1, 2, 3
 # adfft_algo_t
-ALGO_AUTO, ALGO_FOLD, ALGO_BLUESTEIN = 0, 1, 2
+ALGO_AUTO, ALGO_FOLD, ALGO_BLUESTEIN, ALGO_FOUR_STEP = 0, 1, 2, 3
 # adfft_precision_t
 PREC_NATIVE, PREC_FP16X2, PREC_BF16X3 = 0, 1, 2
 
@@ -34,7 +34,8 @@ EXPORTS = (
     "adfft_plan_set_scale", "adfft_plan_set_algorithm", "adfft_plan_set_precision",
     "adfft_plan_get_info", "adfft_plan_workspace_bytes", "adfft_execute",
     "adfft_execute_adjoint", "adfft_execute_host", "adfft_plan_sync_status",
-    "adfft_execute_noalloc",
+    "adfft_execute_noalloc", "adfft_plan_autotune", "adfft_autotune_save", "adfft_autotune_load",
+    "adfft_autotune_clear", "adfft_plan_set_launch_shape",
 )
 
 
@@ -48,7 +49,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("M", ctypes.c_int64), ("batch", ctypes.c_int64),
                 ("dtype", ctypes.c_int32), ("algo", ctypes.c_int32), ("fft_len", ctypes.c_int64),
                 ("residues", ctypes.c_int64), ("fold", ctypes.c_int64), ("cluster", ctypes.c_int32),
-                ("passes", ctypes.c_int32), ("scale", ctypes.c_double)]
+                ("passes", ctypes.c_int32), ("scale", ctypes.c_double), ("staged", ctypes.c_int32),
+                ("tuned", ctypes.c_int32)]
 
 
 _lib = None
@@ -82,6 +84,11 @@ def load(path: str | None = None):
         "adfft_execute_host": ([vp, vp, vp, vp], i32),
         "adfft_plan_sync_status": ([vp, vp], i32),
         "adfft_execute_noalloc": ([i64, i64, i64, i32, vp, vp, vp], i32),
+        "adfft_plan_autotune": ([vp, vp, vp, vp, i32], i32),
+        "adfft_autotune_save": ([ctypes.c_char_p], i32),
+        "adfft_autotune_load": ([ctypes.c_char_p], i32),
+        "adfft_autotune_clear": ([], i32),
+        "adfft_plan_set_launch_shape": ([vp, i64, i32, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -140,6 +147,11 @@ class Plan:
     def set_precision(self, mode):
         _check(self.lib.adfft_plan_set_precision(self._h, int(mode)), "adfft_plan_set_precision")
 
+    def set_launch_shape(self, fft_len=0, cluster=0, staged=-1):
+        _check(self.lib.adfft_plan_set_launch_shape(self._h, int(fft_len), int(cluster), int(staged)),
+               "adfft_plan_set_launch_shape")
+        self.info = self.get_info()
+
     def workspace_bytes(self) -> int:
         return int(self.lib.adfft_plan_workspace_bytes(self._h))
 
@@ -158,6 +170,13 @@ class Plan:
                                            ctypes.c_void_p(_stream_handle(stream))),
                "adfft_execute_host")
 
+    def autotune(self, d_in: int, d_out: int, stream=None, iters=0):
+        """Time the candidate launch shapes on these buffers and keep the fastest (d_out is overwritten)."""
+        _check(self.lib.adfft_plan_autotune(self._h, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
+                                            ctypes.c_void_p(_stream_handle(stream)), int(iters)),
+               "adfft_plan_autotune")
+        self.info = self.get_info()
+
     def sync_status(self, stream=None):
         """Synchronise the stream and raise if a kernel of the plan reported an error."""
         _check(self.lib.adfft_plan_sync_status(self._h, ctypes.c_void_p(_stream_handle(stream))),
@@ -173,6 +192,47 @@ class Plan:
             self.destroy()
         except Exception:
             pass
+
+
+class RaggedPlan(Plan):
+    """adfft_plan_create_ragged: signals of uneven N and alpha packed back to back.
+
+    in_off / out_off (numpy int64, count + 1 entries) are the packed offsets in
+    samples and bins from adfft_plan_offsets.
+    """
+
+    def __init__(self, Ns, alphas, dtype=R32):
+        import numpy as np
+        lib = load()
+        Na = np.ascontiguousarray(np.asarray(Ns, dtype=np.int64))
+        Aa = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+        if Na.shape != Aa.shape or Na.ndim != 1:
+            raise ValueError("Ns and alphas must be 1-D arrays of equal length")
+        h = lib.adfft_plan_create_ragged(Na.ctypes.data_as(ctypes.c_void_p), Aa.ctypes.data_as(ctypes.c_void_p),
+                                         int(Na.size), int(dtype))
+        if not h:
+            raise AdfftError(lib.adfft_last_error(), "adfft_plan_create_ragged")
+        self._h = ctypes.c_void_p(h)
+        self.lib = lib
+        self.info = self.get_info()
+        self.in_off = np.zeros(Na.size + 1, dtype=np.int64)
+        self.out_off = np.zeros(Na.size + 1, dtype=np.int64)
+        _check(lib.adfft_plan_offsets(self._h, self.in_off.ctypes.data_as(ctypes.c_void_p),
+                                      self.out_off.ctypes.data_as(ctypes.c_void_p)), "adfft_plan_offsets")
+
+
+def autotune_save(path):
+    """Write the process-wide tuning cache to a JSON file."""
+    _check(load().adfft_autotune_save(os.fsencode(path)), "adfft_autotune_save")
+
+
+def autotune_load(path):
+    """Merge a tuning-cache file written by autotune_save."""
+    _check(load().adfft_autotune_load(os.fsencode(path)), "adfft_autotune_load")
+
+
+def autotune_clear():
+    _check(load().adfft_autotune_clear(), "adfft_autotune_clear")
 
 
 def execute_noalloc(N, M, batch, dtype, d_in: int, d_out: int, stream=None):

@@ -29,6 +29,14 @@ struct FusedLaunch {
   size_t smem;
 };
 
+// Launch-shape choice of the fused fold path (set by the plan's default rule
+// or by the autotuner).
+struct FoldChoice {
+  int64_t np = 0;    // sub-FFT length: a power of two dividing gcd(Mc, Nc); 0 = the largest such
+  int cluster = 0;   // CTAs per cluster; 0 = the smallest that fits
+  int stage = -1;    // input staging through shared memory: 1 required, 0 never, -1 where it fits
+};
+
 // Launch geometry of the chirp-z kernel.
 struct BluesteinLaunch {
   BluesteinArgs args;
@@ -59,8 +67,14 @@ struct Plan {
   int device = 0;
   size_t in_elem = 0, out_elem = 0;   // bytes per input scalar/complex, per output complex
 
+  int auto_algo = ADFFT_ALGO_FOLD;    // what ADFFT_ALGO_AUTO selects (default rule or autotuner)
+  bool stage_ok = true;               // input staging allowed (bulk copies need 16-byte aligned signals)
+  const long long* d_offs = nullptr;  // ragged sub-plans: device {input byte, output bin} offsets per signal
+  bool tuned = false;                 // launch shape set by the autotuner (or its cache)
+
   // fold + FFT (fused) path
   bool fold_ok = false;
+  FoldChoice fold_choice{};           // the choice p.fused was configured with
   FusedLaunch fused{};
   void* d_tw = nullptr;               // twiddle table of the fused path
   int* d_status = nullptr;            // device status word (0, or ADFFT_ERR_TIMEOUT)
@@ -117,6 +131,23 @@ int fused_values_per_thread(bool dbl);
 cudaError_t adjoint_prepare(const FusedLaunch& L);
 cudaError_t adjoint_launch(const FusedLaunch& L, const void* g, void* xb, cudaStream_t stream);
 size_t adjoint_smem_bytes(const FusedLaunch& L);
+
+// Plan set-up steps (plan.cu).  Each returns ADFFT_OK, ADFFT_ERR_UNSUPPORTED_SIZE
+// when the form does not apply to the plan's sizes, or a CUDA/allocation error.
+void core_shape(const Plan& p, int* mode, int64_t* Nc, int64_t* Mc);
+int setup_fold(Plan& p, const FoldChoice* forced = nullptr);
+int setup_twopass(Plan& p);
+int setup_bluestein(Plan& p);
+void release_twopass(Plan& p);
+int prepare_precision(Plan& p);   // function attributes of the precision-form kernels in use
+int64_t plan_gcd(int64_t a, int64_t b);
+constexpr int kFoldMaxCluster = 16;   // largest cluster the fused kernel is launched with
+constexpr int kTuneMaxFold = 16;      // largest fold factor q the autotuner and default rule consider
+
+// Autotuner (autotune.cu): apply a cached choice at plan creation; time and choose.
+void autotune_apply_cached(Plan& p);
+int autotune_plan(Plan& p, const void* in, void* out, cudaStream_t s, int iters);
+void ragged_invalidate(Plan& p);   // drop captured graphs (launch shapes changed)
 
 // Launch the plan's forward / adjoint kernels (no argument checks).
 int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s);

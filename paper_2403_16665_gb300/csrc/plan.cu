@@ -17,7 +17,7 @@ namespace {
 thread_local int g_last_error = ADFFT_OK;
 
 constexpr size_t kSmemLimit = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
-constexpr int kMaxCluster = 16;             // non-portable cluster size limit
+constexpr int kMaxCluster = kFoldMaxCluster;   // non-portable cluster size limit
 constexpr int kMaxFold = 64;                // largest fold factor q the fused kernel takes
 constexpr int kMaxThreads = 512;
 
@@ -80,15 +80,20 @@ int upload(void** dst, const std::vector<T>& v);
 
 // Configure a fused fold+FFT launch for the complex core of Nc input elements
 // and Mc bins (twiddle modulus Mt); stage_bytes > 0 asks for bulk-copy input
-// staging of that many bytes per signal, used if it fits.  Allocates the
-// twiddle table in *d_tw.  Returns ADFFT_OK or why the shape does not fit.
+// staging of that many bytes per signal, used if it fits.  The choice fixes the
+// sub-FFT length Np, a power of two dividing both Mc and Nc (P = Mc/Np residues
+// and a fold of q = Nc/Np blocks: the identity holds for any common divisor),
+// the cluster size (0: the smallest that fits) and whether staging may be
+// used.  Allocates the twiddle table in *d_tw unless one is passed in.
+// Returns ADFFT_OK or why the shape does not fit.
 int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int64_t batch,
                     int64_t stage_bytes, int max_cluster, double scale, int* status,
-                    FusedLaunch& L, void** d_tw) {
-  const int64_t Np = gcd64(Mc, Nc);
+                    FusedLaunch& L, void** d_tw, const FoldChoice& choice = FoldChoice{}) {
+  const int64_t g = gcd64(Mc, Nc);
+  const int64_t Np = choice.np > 0 ? choice.np : (g & -g);
+  if (!is_pow2(Np) || g % Np) return ADFFT_ERR_UNSUPPORTED_SIZE;
   const int64_t P = Mc / Np, q = Nc / Np;
-  if (!is_pow2(Np)) return ADFFT_ERR_UNSUPPORTED_SIZE;
-  if (q > kMaxFold) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  if (q > kMaxFold || P > (int64_t(1) << 30)) return ADFFT_ERR_UNSUPPORTED_SIZE;
   if (Mt >= (int64_t(1) << 31)) return ADFFT_ERR_UNSUPPORTED_SIZE;
   const size_t esz = dbl ? 16 : 8;
   const int vpt = fused_values_per_thread(dbl);
@@ -98,14 +103,17 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   int lo_n, hi_n;
   const int tw_n = (1 << bits) + (int)((Mt + (1 << bits) - 1) >> bits);
   const int64_t region = Np + Np / 16 + 2;
-  const bool can_stage = stage_bytes > 0 && (stage_bytes % 16) == 0 && stage_bytes <= (int64_t)kSmemLimit;
+  const bool can_stage = choice.stage != 0 && stage_bytes > 0 && (stage_bytes % 16) == 0 &&
+                         stage_bytes <= (int64_t)kSmemLimit;
   int C = -1, stage = 0;
   size_t smem = 0;
   for (int pass = 0; pass < 2 && C < 0; ++pass) {
     if (pass == 0 && !can_stage) continue;
+    if (pass == 1 && choice.stage == 1) continue;
     const int st = (pass == 0) ? (int)stage_bytes : 0;
     for (int c = 1; c <= std::min<int64_t>(P, max_cluster); ++c) {
       if (P % c) continue;
+      if (choice.cluster > 0 && c != choice.cluster) continue;
       const int64_t rpc = P / c;
       if (rpc * Np > max_vals) continue;
       const FusedSmem lay = fused_smem_layout(tw_n, st, (int)rpc, (int)region, (int)esz);
@@ -150,38 +158,45 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   a.divP = make_fastdiv((uint32_t)P);
   a.divRPC = make_fastdiv((uint32_t)RPC);
 
-  // tables
-  size_t tw_bytes;
-  std::vector<unsigned char> host;
-  if (dbl) {
-    auto t = build_two_level<double>(Mt, bits, &lo_n, &hi_n);
-    tw_bytes = t.size() * sizeof(double);
-    host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + tw_bytes);
-  } else {
-    auto t = build_two_level<float>(Mt, bits, &lo_n, &hi_n);
-    tw_bytes = t.size() * sizeof(float);
-    host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + tw_bytes);
-  }
+  // table W_Mt (depends on Mt and the precision only: a table passed in is reused)
+  lo_n = 1 << bits;
+  hi_n = (int)((Mt + lo_n - 1) >> bits);
   a.tw_lo_n = lo_n;
   a.tw_hi_n = hi_n;
-  cudaError_t e = cudaMalloc(d_tw, tw_bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *d_tw = nullptr;
-    return cuda_status(e);
+  if (!*d_tw) {
+    size_t tw_bytes;
+    std::vector<unsigned char> host;
+    if (dbl) {
+      auto t = build_two_level<double>(Mt, bits, &lo_n, &hi_n);
+      tw_bytes = t.size() * sizeof(double);
+      host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + tw_bytes);
+    } else {
+      auto t = build_two_level<float>(Mt, bits, &lo_n, &hi_n);
+      tw_bytes = t.size() * sizeof(float);
+      host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + tw_bytes);
+    }
+    cudaError_t e = cudaMalloc(d_tw, tw_bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *d_tw = nullptr;
+      return cuda_status(e);
+    }
+    e = cudaMemcpy(*d_tw, host.data(), tw_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_status(e);
   }
-  e = cudaMemcpy(*d_tw, host.data(), tw_bytes, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_status(e);
   a.tw = *d_tw;
 
   int threads = (int)((RPC * Np + vpt - 1) / vpt);
+  // the epilogue gives every residue at least one thread of each CTA
+  threads = (int)std::max<int64_t>(threads, P);
   threads = std::max(32, (threads + 31) / 32 * 32);
+  if (threads > kMaxThreads) return ADFFT_ERR_UNSUPPORTED_SIZE;
   L.mode = mode;
   L.dbl = dbl;
   L.threads = threads;
   L.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(batch, 65535));
   L.smem = smem;
-  e = fused_prepare(L);
+  cudaError_t e = fused_prepare(L);
   if (e == cudaSuccess) e = adjoint_prepare(L);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -190,6 +205,8 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   if (C > 1 && fused_max_active_clusters(L) < 1) return ADFFT_ERR_UNSUPPORTED_SIZE;
   return ADFFT_OK;
 }
+
+}  // namespace
 
 // How the plan's input maps onto the complex core: mode, Nc, Mc.
 void core_shape(const Plan& p, int* mode, int64_t* Nc, int64_t* Mc) {
@@ -208,19 +225,41 @@ void core_shape(const Plan& p, int* mode, int64_t* Nc, int64_t* Mc) {
   }
 }
 
-// Configure the fused single-pass fold+FFT path.
-int setup_fold(Plan& p) {
+// Configure the fused single-pass fold+FFT path.  Without a forced choice the
+// sub-FFT length is the largest power of two dividing gcd(Mc, Nc), halved
+// while no cluster fits (and the fold factor stays within kTuneMaxFold), the
+// cluster the smallest that fits, with input staging where it fits.
+int setup_fold(Plan& p, const FoldChoice* forced) {
   int mode;
   int64_t Nc, Mc;
   core_shape(p, &mode, &Nc, &Mc);
   const int64_t Mt = (mode == kLoadRealPacked) ? p.M : Mc;
-  const int64_t sig_bytes = (int64_t)p.N * (int64_t)p.in_elem;
-  int rc = configure_fused(p.dbl, mode, Nc, Mc, Mt, p.batch, sig_bytes, kMaxCluster, p.scale, p.d_status,
-                           p.fused, &p.d_tw);
+  const int64_t sig_bytes = p.stage_ok ? (int64_t)p.N * (int64_t)p.in_elem : 0;
+  const int64_t g = gcd64(Mc, Nc);
+  int rc = ADFFT_ERR_UNSUPPORTED_SIZE;
+  FoldChoice ch{};
+  FusedLaunch L{};   // configured here, taken only on success (the plan keeps its shape otherwise)
+  if (forced) {
+    ch = *forced;
+    rc = configure_fused(p.dbl, mode, Nc, Mc, Mt, p.batch, sig_bytes, kMaxCluster, p.scale, p.d_status,
+                         L, &p.d_tw, ch);
+  } else {
+    const int64_t np0 = g & -g;
+    for (int64_t np = np0; np >= 1; np /= 2) {
+      if (np != np0 && Nc / np > kTuneMaxFold) break;
+      ch = FoldChoice{np, 0, -1};
+      rc = configure_fused(p.dbl, mode, Nc, Mc, Mt, p.batch, sig_bytes, kMaxCluster, p.scale, p.d_status,
+                           L, &p.d_tw, ch);
+      if (rc != ADFFT_ERR_UNSUPPORTED_SIZE) break;
+    }
+  }
   if (rc != ADFFT_OK) return rc;
+  p.fused = L;
   p.fused.args.in_stride = p.N;   // complex elements or real scalars per signal
   p.fused.args.in_unit = (int)p.in_elem;
   p.fused.args.M = p.M;
+  p.fused.args.offs = p.d_offs;
+  p.fold_choice = FoldChoice{p.fused.args.Np, p.fused.args.C, p.fused.args.stage_bytes > 0 ? 1 : 0};
   p.fold_ok = true;
   return ADFFT_OK;
 }
@@ -229,11 +268,9 @@ int setup_fold(Plan& p) {
 int setup_twopass(Plan& p) {
   int mode;
   int64_t Nc, Mc;
+  if (p.tp_ok) return ADFFT_OK;
   core_shape(p, &mode, &Nc, &Mc);
   if (mode == kLoadRealPlain || !is_pow2(Nc) || Nc < 4) return ADFFT_ERR_UNSUPPORTED_SIZE;
-  if (Mc % Nc != 0 && (Mc * 2) % Nc != 0) {
-    // alpha must make R1 = alpha A an integer for some power-of-two A
-  }
   const size_t esz = p.dbl ? 16 : 8;
   const int vpt = fused_values_per_thread(p.dbl);
   for (int max_c : {4, 8}) {
@@ -346,6 +383,8 @@ int setup_twopass(Plan& p) {
           return cuda_status(e);
         }
       }
+      p.tp1.args.offs = p.d_offs;
+      t.f.offs = p.d_offs;
       p.tp_A = A;
       p.tp_B = B;
       p.tp_ok = true;
@@ -354,6 +393,21 @@ int setup_twopass(Plan& p) {
   }
   return ADFFT_ERR_UNSUPPORTED_SIZE;
 }
+
+// Free the two-pass form's tables and workspace (the plan keeps its other forms).
+void release_twopass(Plan& p) {
+  for (void** q : {&p.d_tp_tw1, &p.d_tp_post, &p.d_tp_tw2, &p.d_tp_wM, &p.d_ws}) {
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+  }
+  p.ws_bytes = 0;
+  p.tp_ok = false;
+  p.tp_A = p.tp_B = 0;
+}
+
+int64_t plan_gcd(int64_t a, int64_t b) { return gcd64(a, b); }
+
+namespace {
 
 // In-place iterative radix-2 FFT in double precision (host), forward sign.
 void host_fft(std::vector<std::complex<double>>& a) {
@@ -410,6 +464,8 @@ std::vector<T> flatten(const std::vector<std::complex<double>>& v) {
   }
   return o;
 }
+
+}  // namespace
 
 // Configure the chirp-z path (any N, M); returns ADFFT_OK or why it does not apply.
 int setup_bluestein(Plan& p) {
@@ -489,6 +545,7 @@ int setup_bluestein(Plan& p) {
   b.B = (int)B;
   b.chunks = (int)chunks;
   b.real_in = p.real ? 1 : 0;
+  a.offs = p.d_offs;
   BL.r0 = 1 << lr0;
   BL.dbl = p.dbl;
   BL.threads = std::max(32, (int)((L / vpt + 31) / 32 * 32));
@@ -503,7 +560,6 @@ int setup_bluestein(Plan& p) {
   return ADFFT_OK;
 }
 
-}  // namespace
 
 int cuda_status_of(cudaError_t e) { return cuda_status(e); }
 
@@ -513,15 +569,17 @@ int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s) {
   const bool f16 = p.precision == ADFFT_PREC_FP16X2;
   if (p.algo == ADFFT_ALGO_BLUESTEIN) {
     e = bluestein_launch(p.blu, in, out, s);
-  } else if (p.fold_ok) {
+  } else if (p.algo == ADFFT_ALGO_FOLD && p.fold_ok) {
     e = !tc ? fused_launch(p.fused, in, out, s)
             : f16 ? tc_launch_fused_fp16(p.fused, in, out, s) : tc_launch_fused_bf16(p.fused, in, out, s);
-  } else {
+  } else if (p.tp_ok) {
     e = !tc ? fused_launch(p.tp1, in, p.d_ws, s)
             : f16 ? tc_launch_fused_fp16(p.tp1, in, p.d_ws, s) : tc_launch_fused_bf16(p.tp1, in, p.d_ws, s);
     if (e == cudaSuccess)
       e = !tc ? twopass_launch(p.tp2, p.d_ws, out, s)
               : f16 ? tc_launch_columns_fp16(p.tp2, p.d_ws, out, s) : tc_launch_columns_bf16(p.tp2, p.d_ws, out, s);
+  } else {
+    return ADFFT_ERR_NOT_SUPPORTED;
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -532,15 +590,30 @@ int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s) {
 
 int launch_adjoint(Plan& p, const void* g, void* xb, cudaStream_t s) {
   cudaError_t e;
-  if (p.fold_ok) {
+  // the selected fold form, else whichever fold form the plan has (the chirp-z form has no adjoint kernel)
+  const bool use_tp = p.tp_ok && (p.algo == ADFFT_ALGO_FOUR_STEP || !p.fold_ok);
+  if (!use_tp && p.fold_ok) {
     e = adjoint_launch(p.fused, g, xb, s);
-  } else if (p.tp_ok) {
+  } else if (use_tp) {
     // transpose of the two passes, in reverse order, through the same workspace
     e = twopass_adjoint_launch(p.tp2, g, p.d_ws, s);
     if (e == cudaSuccess) e = adjoint_launch(p.tp1, p.d_ws, xb, s);
   } else {
-    return ADFFT_ERR_NOT_SUPPORTED;   // the chirp-z form has no adjoint kernel
+    return ADFFT_ERR_NOT_SUPPORTED;
   }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  return ADFFT_OK;
+}
+
+int prepare_precision(Plan& p) {
+  if (p.precision == ADFFT_PREC_NATIVE) return ADFFT_OK;
+  const bool f16 = p.precision == ADFFT_PREC_FP16X2;
+  cudaError_t e = cudaSuccess;
+  if (p.fold_ok) e = f16 ? tc_prepare_fp16(&p.fused, nullptr) : tc_prepare_bf16(&p.fused, nullptr);
+  if (e == cudaSuccess && p.tp_ok) e = f16 ? tc_prepare_fp16(&p.tp1, &p.tp2) : tc_prepare_bf16(&p.tp1, &p.tp2);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_status(e);
@@ -645,9 +718,12 @@ adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dty
     const int rc_blu = setup_bluestein(p);
     if (rc_blu != ADFFT_OK && rc_blu != ADFFT_ERR_UNSUPPORTED_SIZE) return fail(rc_blu, h);
   }
-  if (p.fold_ok || p.tp_ok) p.algo = ADFFT_ALGO_FOLD;
+  if (p.fold_ok) p.algo = ADFFT_ALGO_FOLD;
+  else if (p.tp_ok) p.algo = ADFFT_ALGO_FOUR_STEP;
   else if (p.blu_ok) p.algo = ADFFT_ALGO_BLUESTEIN;
   else return fail(ADFFT_ERR_UNSUPPORTED_SIZE, h);
+  p.auto_algo = p.algo;
+  autotune_apply_cached(p);   // a launch shape recorded by the autotuner for these sizes, if any
   g_last_error = ADFFT_OK;
   return h;
 }
@@ -707,28 +783,48 @@ int adfft_plan_set_scale(adfft_plan_t plan, double S) {
 }
 
 int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
+  using namespace adfft;
   if (!plan) return ADFFT_ERR_INVALID_ARG;
   Plan& p = plan->p;
   if (p.ragged) return (algo == ADFFT_ALGO_AUTO) ? ADFFT_OK : ADFFT_ERR_NOT_SUPPORTED;
   if (algo == ADFFT_ALGO_AUTO) {
-    p.algo = (p.fold_ok || p.tp_ok) ? ADFFT_ALGO_FOLD : ADFFT_ALGO_BLUESTEIN;
+    p.algo = p.auto_algo;
     return ADFFT_OK;
   }
   if (algo == ADFFT_ALGO_FOLD) {
+    // the single-pass fold form, else (sub-FFT beyond one cluster) its two-pass variant
     if (!p.fold_ok && !p.tp_ok) return ADFFT_ERR_NOT_SUPPORTED;
-    p.algo = algo;
+    p.algo = p.fold_ok ? ADFFT_ALGO_FOLD : ADFFT_ALGO_FOUR_STEP;
     return ADFFT_OK;
   }
-  if (algo == ADFFT_ALGO_BLUESTEIN) {
-    if (!p.blu_ok) {
-      const int rc = adfft::setup_bluestein(p);
-      if (rc == ADFFT_ERR_UNSUPPORTED_SIZE) return ADFFT_ERR_NOT_SUPPORTED;
-      if (rc != ADFFT_OK) return rc;
-    }
-    p.algo = algo;
-    return ADFFT_OK;
+  int rc = ADFFT_OK;
+  if (algo == ADFFT_ALGO_FOUR_STEP) {
+    rc = setup_twopass(p);
+    if (rc == ADFFT_OK) rc = prepare_precision(p);
+  } else if (algo == ADFFT_ALGO_BLUESTEIN) {
+    rc = setup_bluestein(p);
+  } else {
+    return ADFFT_ERR_INVALID_ARG;
   }
-  return ADFFT_ERR_INVALID_ARG;
+  if (rc == ADFFT_ERR_UNSUPPORTED_SIZE) return ADFFT_ERR_NOT_SUPPORTED;
+  if (rc != ADFFT_OK) return rc;
+  p.algo = algo;
+  return ADFFT_OK;
+}
+
+int adfft_plan_set_launch_shape(adfft_plan_t plan, int64_t fft_len, int cluster, int staged) {
+  using namespace adfft;
+  if (!plan || fft_len < 0 || cluster < 0 || cluster > kFoldMaxCluster || staged < -1 || staged > 1)
+    return ADFFT_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  if (p.ragged) return ADFFT_ERR_NOT_SUPPORTED;
+  FoldChoice c{fft_len, cluster, staged};
+  int rc = setup_fold(p, &c);
+  if (rc == ADFFT_OK) rc = prepare_precision(p);
+  if (rc == ADFFT_ERR_UNSUPPORTED_SIZE) return ADFFT_ERR_NOT_SUPPORTED;
+  if (rc != ADFFT_OK) return rc;
+  p.algo = ADFFT_ALGO_FOLD;
+  return ADFFT_OK;
 }
 
 int adfft_plan_set_precision(adfft_plan_t plan, int mode) {
@@ -742,15 +838,11 @@ int adfft_plan_set_precision(adfft_plan_t plan, int mode) {
   if (mode != ADFFT_PREC_FP16X2 && mode != ADFFT_PREC_BF16X3) return ADFFT_ERR_INVALID_ARG;
   // tensor-core radix-16 passes: complex64 data in the fold forms (not chirp-z, not ragged)
   if (p.dbl || p.ragged || (!p.fold_ok && !p.tp_ok)) return ADFFT_ERR_NOT_SUPPORTED;
-  const FusedLaunch* L1 = p.fold_ok ? &p.fused : &p.tp1;
-  const TwoPassLaunch* L2 = p.fold_ok ? nullptr : &p.tp2;
-  cudaError_t e = (mode == ADFFT_PREC_FP16X2) ? tc_prepare_fp16(L1, L2) : tc_prepare_bf16(L1, L2);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cuda_status(e);
-  }
+  const int old = p.precision;
   p.precision = mode;
-  return ADFFT_OK;
+  const int rc = prepare_precision(p);
+  if (rc != ADFFT_OK) p.precision = old;
+  return rc;
 }
 
 int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
@@ -769,9 +861,14 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
     info->fold = 0;
     info->cluster = 0;
     int passes = 1;
-    for (auto* sp : p.r_sub) passes = std::max(passes, (!sp->p.fold_ok && sp->p.tp_ok) ? 2 : 1);
+    bool tuned = !p.r_sub.empty();
+    for (auto* sp : p.r_sub) {
+      passes = std::max(passes, sp->p.algo == ADFFT_ALGO_FOUR_STEP ? 2 : 1);
+      tuned = tuned && sp->p.tuned;
+    }
     info->passes = passes;
     info->scale = 0.0;
+    info->tuned = tuned ? 1 : 0;
     return ADFFT_OK;
   }
   if (p.algo == ADFFT_ALGO_BLUESTEIN) {
@@ -779,7 +876,7 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
     info->residues = p.blu.args.chunks;
     info->fold = 0;
     info->cluster = 1;
-  } else if (!p.fold_ok && p.tp_ok) {
+  } else if (p.algo == ADFFT_ALGO_FOUR_STEP) {
     info->fft_len = p.tp_A * p.tp_B;      // the sub-FFT length, split A x B over two passes
     info->residues = p.tp1.args.P;
     info->fold = p.tp1.args.q;
@@ -790,8 +887,10 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
     info->fold = p.fused.args.q;
     info->cluster = p.fused.args.C;
   }
-  info->passes = (!p.fold_ok && p.tp_ok && p.algo == ADFFT_ALGO_FOLD) ? 2 : 1;
+  info->passes = (p.algo == ADFFT_ALGO_FOUR_STEP) ? 2 : 1;
   info->scale = p.scale;
+  info->staged = (p.algo == ADFFT_ALGO_FOLD && p.fused.args.stage_bytes > 0) ? 1 : 0;
+  info->tuned = p.tuned ? 1 : 0;
   return ADFFT_OK;
 }
 
@@ -863,14 +962,36 @@ int adfft_plan_sync_status(adfft_plan_t plan, void* stream) {
   if (!plan) return ADFFT_ERR_INVALID_ARG;
   Plan& p = plan->p;
   cudaStream_t s = (cudaStream_t)stream;
+  if (p.ragged) {
+    // the shape classes' kernels report into their sub-plans' status words
+    int rc = ADFFT_OK;
+    for (auto* sp : p.r_sub) {
+      const int r = adfft_plan_sync_status(sp, stream);
+      if (rc == ADFFT_OK) rc = r;
+    }
+    if (p.r_sub.empty()) {
+      const cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e);
+      }
+    }
+    return rc;
+  }
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_status(e);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
   if (h != 0) {
     e = cudaMemsetAsync(p.d_status, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
     return h == kStatusTimeout ? ADFFT_ERR_TIMEOUT : ADFFT_ERR_CUDA;
   }
   return ADFFT_OK;

@@ -23,6 +23,7 @@ namespace adfft {
 namespace {
 
 void set_offsets(Plan& sub, const long long* d_offs) {
+  sub.d_offs = d_offs;
   sub.fused.args.offs = d_offs;
   sub.blu.args.f.offs = d_offs;
   sub.tp1.args.offs = d_offs;
@@ -86,6 +87,8 @@ int capture(Plan& p, const void* in, void* out, int which) {
 }
 
 }  // namespace
+
+void ragged_invalidate(Plan& p) { destroy_graphs(p); }
 
 void ragged_release(Plan& p) {
   destroy_graphs(p);
@@ -192,7 +195,17 @@ adfft_plan_s* ragged_create(const int64_t* N, const double* alpha, int64_t count
     }
     p.r_offs.push_back(d);
     set_offsets(sub->p, static_cast<const long long*>(d));
-    if (!stage_ok) sub->p.fused.args.stage_bytes = 0;   // bulk copies need 16-byte aligned sources
+    if (!stage_ok) {
+      // bulk copies need 16-byte aligned sources: re-plan the class without input staging
+      sub->p.stage_ok = false;
+      if (sub->p.fold_ok && sub->p.fused.args.stage_bytes > 0) {
+        FoldChoice c = sub->p.fold_choice;
+        c.stage = 0;
+        c.cluster = 0;
+        const int rc = setup_fold(sub->p, &c);
+        if (rc != ADFFT_OK) return bail(rc);
+      }
+    }
   }
   for (int k = 0; k < kRaggedStreams; ++k) {
     if (cudaStreamCreateWithFlags(&p.r_streams[k], cudaStreamNonBlocking) != cudaSuccess ||

@@ -78,8 +78,9 @@ def test_complex_workload_forced_chirp_z(alpha):
     assert d.max() <= 2 * tol_for(M, False)
 
 
-@pytest.mark.parametrize("N,M", [(1000, 2000), (1000, 2500), (999, 3996), (100, 250)])
-def test_auto_picks_chirp_z_when_gcd_is_not_a_power_of_two(N, M):
+@pytest.mark.parametrize("N,M", [(1000, 2000), (1000, 2500), (999, 3996), (300, 750)])
+def test_auto_picks_chirp_z_when_no_power_of_two_divisor_gives_a_small_fold(N, M):
+    """Every power-of-two divisor g' of gcd(M, N) leaves a fold N/g' > 64 here."""
     _torch()
     for code in (adfft.R32, adfft.C64):
         assert adfft.Plan(N, batch=1, dtype=code, M=M).info.algo == adfft.ALGO_BLUESTEIN

@@ -1,5 +1,6 @@
-"""GPU parity of the two-pass (four-step) form used when the sub-FFT length
-exceeds one cluster's shared memory, against the FP64 oracle on sampled bins."""
+"""GPU parity of the two-pass (four-step) form, used when no single-pass shape
+fits one cluster's shared memory and selectable by hand otherwise, against the
+FP64 oracle on sampled bins."""
 import numpy as np
 import pytest
 
@@ -24,11 +25,13 @@ def tol_for(M, dbl):
 NP = {adfft.R32: np.float32, adfft.R64: np.float64, adfft.C64: np.complex64, adfft.C128: np.complex128}
 
 
-def run(torch, x, M, code):
+def run(torch, x, M, code, four_step=False):
     dev = torch.device("cuda:0")
     xt = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     B, N = xt.shape
     plan = adfft.Plan(N, batch=B, dtype=code, M=M)
+    if four_step:
+        plan.set_algorithm(adfft.ALGO_FOUR_STEP)
     dbl = code in (adfft.R64, adfft.C128)
     X = torch.empty((B, M), dtype=torch.complex128 if dbl else torch.complex64, device=dev)
     plan.execute(xt.data_ptr(), X.data_ptr())
@@ -37,10 +40,24 @@ def run(torch, x, M, code):
 
 
 def expected_passes(code, N, M):
+    """1 if the default rule finds a single-pass shape: a power-of-two sub-FFT
+    length Np dividing gcd(Mc, Nc) (the largest with a fold q <= 64, smaller
+    ones with q <= 16) whose P = Mc/Np residues spread over a cluster of at
+    most 16 CTAs of 16384 (fp64: 8192) values each; else 2."""
     real = code in (adfft.R32, adfft.R64)
     Nc, Mc = (N // 2, M // 2) if real else (N, M)
-    limit = 8192 if code in (adfft.R64, adfft.C128) else 16384
-    return 2 if np.gcd(Nc, Mc) > limit else 1
+    vals = 8192 if code in (adfft.R64, adfft.C128) else 16384
+    g = int(np.gcd(Nc, Mc))
+    np0 = g & -g
+    n = np0
+    while n >= 1:
+        q, P = Nc // n, Mc // n
+        if q > (64 if n == np0 else 16):
+            break
+        if any(P % c == 0 and (P // c) * n <= vals and P <= 512 for c in range(1, min(16, P) + 1)):
+            return 1
+        n //= 2
+    return 2
 
 
 def sample_bins(M, n, seed):
@@ -49,10 +66,11 @@ def sample_bins(M, n, seed):
                                      rng.integers(0, M, n)]))
 
 
+@pytest.mark.parametrize("four_step", [False, True])
 @pytest.mark.parametrize("code", [adfft.R32, adfft.C64, adfft.R64, adfft.C128])
 @pytest.mark.parametrize("N,alpha", [(1 << 15, 2), (1 << 16, 4), (1 << 17, 8), (1 << 16, 2.5),
                                      (1 << 18, 16), (1 << 15, 3)])
-def test_two_pass_sampled(code, N, alpha):
+def test_two_pass_sampled(code, N, alpha, four_step):
     torch = _torch()
     M = int(round(alpha * N))
     rng = np.random.default_rng(N + M)
@@ -60,13 +78,11 @@ def test_two_pass_sampled(code, N, alpha):
     if code in (adfft.C64, adfft.C128):
         x = x + 1j * rng.standard_normal((2, N))
     x = x.astype(NP[code])
-    X, plan = run(torch, x, M, code)
-    real = code in (adfft.R32, adfft.R64)
-    Nc, Mc = (N // 2, M // 2) if real else (N, M)
-    limit = 8192 if code in (adfft.R64, adfft.C128) else 16384
-    expect = 2 if np.gcd(Nc, Mc) > limit else 1
+    X, plan = run(torch, x, M, code, four_step)
+    expect = 2 if four_step else expected_passes(code, N, M)
     assert plan.info.passes == expect, (plan.info.passes, plan.info.fft_len)
     assert (plan.workspace_bytes() > 0) == (expect == 2)
+    assert plan.info.algo == (adfft.ALGO_FOUR_STEP if expect == 2 else adfft.ALGO_FOLD)
     bins = sample_bins(M, 600, N)
     got = X[:, torch.from_numpy(bins).cuda()].cpu().numpy()
     ref = oracle.alpha_dft(x.astype(np.complex128), M, bins=bins)
@@ -107,7 +123,8 @@ def test_two_pass_adjoint_matches_oracle(code, N, alpha):
     g = (rng.standard_normal((1, M)) + 1j * rng.standard_normal((1, M)))
     dev = torch.device("cuda:0")
     plan = adfft.Plan(N, batch=1, dtype=code, M=M)
-    assert plan.info.passes == expected_passes(code, N, M) == 2
+    plan.set_algorithm(adfft.ALGO_FOUR_STEP)
+    assert plan.info.passes == 2
     gt = torch.from_numpy(g).to(dev)
     xb = torch.empty((1, N), dtype=torch.float64 if real else torch.complex128, device=dev)
     plan.execute_adjoint(gt.data_ptr(), xb.data_ptr())
@@ -117,9 +134,10 @@ def test_two_pass_adjoint_matches_oracle(code, N, alpha):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-12
 
 
+@pytest.mark.parametrize("four_step", [False, True])
 @pytest.mark.parametrize("code,N,alpha", [(adfft.R32, 1 << 17, 8), (adfft.C64, 1 << 15, 3),
                                           (adfft.R32, 1 << 17, 2.5), (adfft.R32, 1 << 22, 16)])
-def test_two_pass_adjoint_dot_product(code, N, alpha):
+def test_two_pass_adjoint_dot_product(code, N, alpha, four_step):
     """<A x, g> = <x, A^H g> through the forward and adjoint two-pass launches."""
     torch = _torch()
     M = int(round(alpha * N))
@@ -132,7 +150,9 @@ def test_two_pass_adjoint_dot_product(code, N, alpha):
         x = torch.randn((1, N), device=dev, generator=gen, dtype=torch.complex64)
     g = torch.randn((1, M), device=dev, generator=gen, dtype=torch.complex64)
     plan = adfft.Plan(N, batch=1, dtype=code, M=M)
-    assert plan.info.passes == expected_passes(code, N, M)
+    if four_step:
+        plan.set_algorithm(adfft.ALGO_FOUR_STEP)
+    assert plan.info.passes == (2 if four_step else expected_passes(code, N, M))
     X = torch.empty((1, M), dtype=torch.complex64, device=dev)
     xb = torch.empty_like(x)
     plan.execute(x.data_ptr(), X.data_ptr())
