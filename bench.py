@@ -4,7 +4,8 @@ One step = one forward transform (fold + twiddle + Stockham FFT + interleaved
 epilogue, one kernel launch) of the whole batch: 4096 real fp32 signals,
 N = 16384, alpha = 8, 131072 complex64 bins each (off-bin tones plus Gaussian
 noise).  Inputs (256 MiB) and outputs (4 GiB) are far larger than the 129 MB
-L2, so no flush is needed between timed steps.
+L2, so no flush is needed between timed steps.  Before warm-up the plan's launch
+shape is chosen by the library's autotuner (adfft_plan_autotune, untimed).
 
     python bench.py [--gpus N --steps K --warmup W] [--impl native|reference]
 
@@ -53,16 +54,21 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kname, khash):
-    """dram read+write bytes per launch recorded from ncu for this exact kernel source."""
+def recorded_traffic(kname, khash, shape):
+    """dram read+write bytes per launch recorded from ncu for this exact kernel source and launch shape."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kname and parts[1] == khash:
+        if (len(parts) >= 5 and not line.startswith("#") and parts[0] == kname and parts[1] == khash
+                and parts[4] == shape):
             return float(parts[2])
     return None
+
+
+def shape_tag(info):
+    return "fft_len=%d,cluster=%d,staged=%d" % (info.fft_len, info.cluster, info.staged)
 
 
 def measured_peaks():
@@ -203,6 +209,10 @@ def run_native(args):
     X = torch.empty((B, M), dtype=torch.complex64, device=dev)
     plan = adfft.Plan(N, batch=B, dtype=adfft.R32, M=M)
     stream = torch.cuda.current_stream(dev)
+    # launch shape chosen by the library's autotuner on this GPU (untimed set-up, like plan creation)
+    if not args.no_tune:
+        plan.autotune(x.data_ptr(), X.data_ptr(), stream, iters=5)
+    info = plan.info
 
     def step():
         plan.execute(x.data_ptr(), X.data_ptr(), stream)
@@ -253,7 +263,7 @@ def run_native(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
     khash = kernel_hash()
-    traffic = recorded_traffic("fused_forward_kernel", khash)
+    traffic = recorded_traffic("fused_forward_kernel", khash, shape_tag(info)) if info.passes == 1 else None
 
     # end to end through adfft_execute_host: pinned host input -> device -> spectrum -> host
     e2e = None
@@ -291,7 +301,11 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(WORKLOAD, parallelism="independent replicas, one batch per GPU"),
+            "config": dict(WORKLOAD, parallelism="independent replicas, one batch per GPU",
+                           launch_shape={"algo": "fold" if info.passes == 1 else "four-step",
+                                         "fft_len": info.fft_len, "residues": info.residues,
+                                         "cluster": info.cluster, "staged": info.staged,
+                                         "autotuned": bool(info.tuned)}),
             "error_vs_fp64": err,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -300,7 +314,7 @@ def run_native(args):
             "cpu_baseline": cpu,
             "clocks": clk,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * info.passes,
         }
         print(json.dumps(line), flush=True)
     plan.destroy()
@@ -317,6 +331,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune", action="store_true", help="keep the plan's default launch shape")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

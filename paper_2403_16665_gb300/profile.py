@@ -32,6 +32,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--prec", type=int, default=adfft.PREC_NATIVE, help="0 native, 1 fp16x2, 2 bf16x3")
     ap.add_argument("--tune", action="store_true", help="autotune the plan first (adfft_plan_autotune)")
+    ap.add_argument("--shape", default=None,
+                    help="fold launch shape fft_len,cluster,staged (adfft_plan_set_launch_shape)")
     args = ap.parse_args()
     _build.build()
     if args.workload == "ragged_r32":
@@ -56,6 +58,9 @@ def main():
     if args.prec != adfft.PREC_NATIVE:
         plan.set_precision(args.prec)
     X = torch.empty((B, M), dtype=adfft.out_dtype(x.dtype), device=dev)
+    if args.shape:
+        fl, cl, st = (int(v) for v in args.shape.split(","))
+        plan.set_launch_shape(fl, cl, st)
     if args.tune:
         plan.autotune(x.data_ptr(), X.data_ptr())
     g = torch.empty_like(x) if args.adjoint else None
