@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
         reinterpret_cast<V*>(obase + sig_in_bytes(a, sig))[n] = acc;
       }
     }
-    if (a.C > 1) cluster_arrive(); else __syncthreads();
+    if (a.C > 1) cluster_arrive_relaxed(); else __syncthreads();
   }
   if (a.C > 1 && (long long)blockIdx.y < a.batch) cluster_wait();
 }

@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     }
     // this CTA has read what it needs from the cluster; the wait that pairs with
     // this arrive comes before the next signal overwrites shared memory
-    if (a.C > 1) cluster_arrive(); else __syncthreads();
+    if (a.C > 1) cluster_arrive_relaxed(); else __syncthreads();
   }
   if (a.C > 1 && (long long)blockIdx.y < a.batch) cluster_wait();
   // a copy can only still be in flight after a timed-out wait: give it time to land
