@@ -68,7 +68,7 @@ def recorded_traffic(kname, khash, shape):
 
 
 def shape_tag(info):
-    return "fft_len=%d,cluster=%d,staged=%d" % (info.fft_len, info.cluster, info.staged)
+    return "fft_len=%d,cluster=%d,staged=%d,grid=%d" % (info.fft_len, info.cluster, info.staged, info.grid)
 
 
 def measured_peaks():
@@ -305,7 +305,7 @@ def run_native(args):
                            launch_shape={"algo": "fold" if info.passes == 1 else "four-step",
                                          "fft_len": info.fft_len, "residues": info.residues,
                                          "cluster": info.cluster, "staged": info.staged,
-                                         "autotuned": bool(info.tuned)}),
+                                         "clusters_launched": info.grid, "autotuned": bool(info.tuned)}),
             "error_vs_fp64": err,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

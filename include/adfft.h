@@ -105,6 +105,8 @@ typedef struct {
     int32_t staged;       /* 1 if the fused pass stages each signal through shared memory */
     int32_t tuned;        /* 1 if the launch shape came from the autotuner or its cache
                              (ragged plans: every shape class) */
+    int32_t grid;         /* clusters the (first) kernel launches; each loops over signals */
+    int32_t reserved;
 } adfft_plan_info_t;
 
 /*
@@ -206,12 +208,13 @@ int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *s
  * power-of-two sub-FFT g' dividing gcd(M, N) (halved for real input) whose
  * P' = M/g' residues fit one cluster's shared memory, with a fold of at most
  * 16 blocks (the fold identity holds for every divisor of the gcd), the
- * smallest such cluster, and input staging where it fits; the two-pass form
- * only where no single-pass shape fits.
+ * smallest such cluster, input staging where it fits, and as many clusters as
+ * can be resident at once, each looping over signals; the two-pass form only
+ * where no single-pass shape fits.
  *
  * adfft_plan_autotune times the forward transform of the plan for every
- * candidate launch shape (sub-FFT length, cluster size, input staging; the
- * two-pass form where it applies) with `iters` timed launches each (1..100;
+ * candidate launch shape (sub-FFT length, cluster size, input staging, a
+ * resident-size or one-per-signal grid; the two-pass form where it applies) with `iters` timed launches each (1..100;
  * 0 means 3) on the caller's buffers, keeps the fastest, and records it in
  * the process-wide tuning cache under (GPU name, driver version, N, M, batch,
  * dtype, precision).  d_in and d_out are as for adfft_execute (d_out is
@@ -234,11 +237,13 @@ int adfft_plan_autotune(adfft_plan_t plan, const void *d_in, void *d_out, void *
  * fft_len = the sub-FFT length g' (a power of two dividing M and N, halved for
  * real input; 0 = the largest such), cluster = CTAs per signal (0 = the
  * smallest that fits), staged = 1 to stage each signal through shared memory,
- * 0 not to, -1 where it fits.  Selects the fold algorithm.  Returns
+ * 0 not to, -1 where it fits; grid = clusters launched: 0 = as many as can be
+ * resident at once, each looping over signals (the default), -1 = one per
+ * signal, n > 0 = at most n.  Selects the fold algorithm.  Returns
  * ADFFT_ERR_NOT_SUPPORTED (the plan unchanged) when the shape does not fit
  * one cluster or the plan has no fold form (ragged, or chirp-z only sizes).
  */
-int adfft_plan_set_launch_shape(adfft_plan_t plan, int64_t fft_len, int cluster, int staged);
+int adfft_plan_set_launch_shape(adfft_plan_t plan, int64_t fft_len, int cluster, int staged, int grid);
 int adfft_autotune_save(const char *path);
 int adfft_autotune_load(const char *path);
 int adfft_autotune_clear(void);

@@ -50,7 +50,7 @@ class PlanInfo(ctypes.Structure):
                 ("dtype", ctypes.c_int32), ("algo", ctypes.c_int32), ("fft_len", ctypes.c_int64),
                 ("residues", ctypes.c_int64), ("fold", ctypes.c_int64), ("cluster", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("scale", ctypes.c_double), ("staged", ctypes.c_int32),
-                ("tuned", ctypes.c_int32)]
+                ("tuned", ctypes.c_int32), ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -88,7 +88,7 @@ def load(path: str | None = None):
         "adfft_autotune_save": ([ctypes.c_char_p], i32),
         "adfft_autotune_load": ([ctypes.c_char_p], i32),
         "adfft_autotune_clear": ([], i32),
-        "adfft_plan_set_launch_shape": ([vp, i64, i32, i32], i32),
+        "adfft_plan_set_launch_shape": ([vp, i64, i32, i32, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -147,8 +147,8 @@ class Plan:
     def set_precision(self, mode):
         _check(self.lib.adfft_plan_set_precision(self._h, int(mode)), "adfft_plan_set_precision")
 
-    def set_launch_shape(self, fft_len=0, cluster=0, staged=-1):
-        _check(self.lib.adfft_plan_set_launch_shape(self._h, int(fft_len), int(cluster), int(staged)),
+    def set_launch_shape(self, fft_len=0, cluster=0, staged=-1, grid=0):
+        _check(self.lib.adfft_plan_set_launch_shape(self._h, int(fft_len), int(cluster), int(staged), int(grid)),
                "adfft_plan_set_launch_shape")
         self.info = self.get_info()
 

@@ -35,6 +35,8 @@ struct FoldChoice {
   int64_t np = 0;    // sub-FFT length: a power of two dividing gcd(Mc, Nc); 0 = the largest such
   int cluster = 0;   // CTAs per cluster; 0 = the smallest that fits
   int stage = -1;    // input staging through shared memory: 1 required, 0 never, -1 where it fits
+  int grid = 0;      // clusters launched: 0 = as many as can be resident at once (each loops over
+                     // signals), -1 = one per signal, > 0 = that many
 };
 
 // Launch geometry of the chirp-z kernel.

@@ -5,7 +5,8 @@
 // Candidates of the fold form: every sub-FFT length Np (a power of two dividing
 // gcd(Mc, Nc), down to 64 while the fold factor q = Nc/Np stays within
 // kTuneMaxFold), every cluster size that divides P = Mc/Np and holds P/C
-// residue FFTs in one CTA's shared memory, with and without input staging.
+// residue FFTs in one CTA's shared memory, with and without input staging,
+// with a resident-size (persistent) grid or one cluster per signal.
 // The two-pass form is a further candidate where it applies.  Every candidate
 // is a configuration the same kernels take at any size: tuning changes which
 // shape runs, never what is computed (results agree to rounding).
@@ -103,7 +104,8 @@ std::vector<FoldChoice> fold_candidates(const Plan& p) {
     const int64_t P = Mc / np;
     for (int c = 1; c <= kFoldMaxCluster && c <= P; ++c) {
       if (P % c || (P / c) * np > vals) continue;
-      for (int st : {1, 0}) out.push_back(FoldChoice{np, c, st});
+      for (int st : {1, 0})
+        for (int grid : {0, -1}) out.push_back(FoldChoice{np, c, st, grid});
     }
   }
   return out;
@@ -273,12 +275,14 @@ bool parse_entry(Parser& ps, Key& k, Entry& en) {
     else if (name == "fft_len") en.fold.np = (int64_t)v, have |= 64;
     else if (name == "cluster") en.fold.cluster = (int)v, have |= 128;
     else if (name == "staged") en.fold.stage = (int)v, have |= 256;
+    else if (name == "grid") en.fold.grid = (int)v;
     else if (name == "ms") en.ms = v;
   } while (ps.eat(','));
   if (!ps.eat('}')) return false;
   if (!have_dev || have != 511) return false;
   if (en.algo != ADFFT_ALGO_FOLD && en.algo != ADFFT_ALGO_FOUR_STEP) return false;
   if (en.fold.stage != 0 && en.fold.stage != 1) return false;
+  if (en.fold.grid < -1) return false;
   return true;
 }
 
@@ -363,9 +367,10 @@ int adfft_autotune_save(const char* path) {
       char buf[512];
       snprintf(buf, sizeof buf,
                ", \"N\": %lld, \"M\": %lld, \"batch\": %lld, \"dtype\": %d, \"precision\": %d, "
-               "\"algo\": %d, \"fft_len\": %lld, \"cluster\": %d, \"staged\": %d, \"ms\": %.6g}",
+               "\"algo\": %d, \"fft_len\": %lld, \"cluster\": %d, \"staged\": %d, \"grid\": %d, "
+               "\"ms\": %.6g}",
                (long long)k.N, (long long)k.M, (long long)k.batch, k.dtype, k.precision, e.algo,
-               (long long)e.fold.np, e.fold.cluster, e.fold.stage == 1 ? 1 : 0, e.ms);
+               (long long)e.fold.np, e.fold.cluster, e.fold.stage == 1 ? 1 : 0, e.fold.grid, e.ms);
       o += buf;
     }
   }

@@ -202,7 +202,12 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
     cudaGetLastError();
     return cuda_status(e);
   }
-  if (C > 1 && fused_max_active_clusters(L) < 1) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  const int resident = fused_max_active_clusters(L);
+  if (C > 1 && resident < 1) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  // persistent grid: clusters loop over signals, so the table load and launch are paid once
+  // per cluster and the next signal's input is fetched while the current one is transformed
+  if (choice.grid > 0) L.grid_y = (int)std::min<int64_t>(L.grid_y, choice.grid);
+  else if (choice.grid == 0 && resident > 0) L.grid_y = std::min(L.grid_y, resident);
   return ADFFT_OK;
 }
 
@@ -259,7 +264,7 @@ int setup_fold(Plan& p, const FoldChoice* forced) {
   p.fused.args.in_unit = (int)p.in_elem;
   p.fused.args.M = p.M;
   p.fused.args.offs = p.d_offs;
-  p.fold_choice = FoldChoice{p.fused.args.Np, p.fused.args.C, p.fused.args.stage_bytes > 0 ? 1 : 0};
+  p.fold_choice = FoldChoice{p.fused.args.Np, p.fused.args.C, p.fused.args.stage_bytes > 0 ? 1 : 0, ch.grid};
   p.fold_ok = true;
   return ADFFT_OK;
 }
@@ -812,13 +817,13 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
   return ADFFT_OK;
 }
 
-int adfft_plan_set_launch_shape(adfft_plan_t plan, int64_t fft_len, int cluster, int staged) {
+int adfft_plan_set_launch_shape(adfft_plan_t plan, int64_t fft_len, int cluster, int staged, int grid) {
   using namespace adfft;
-  if (!plan || fft_len < 0 || cluster < 0 || cluster > kFoldMaxCluster || staged < -1 || staged > 1)
+  if (!plan || fft_len < 0 || cluster < 0 || cluster > kFoldMaxCluster || staged < -1 || staged > 1 || grid < -1)
     return ADFFT_ERR_INVALID_ARG;
   Plan& p = plan->p;
   if (p.ragged) return ADFFT_ERR_NOT_SUPPORTED;
-  FoldChoice c{fft_len, cluster, staged};
+  FoldChoice c{fft_len, cluster, staged, grid};
   int rc = setup_fold(p, &c);
   if (rc == ADFFT_OK) rc = prepare_precision(p);
   if (rc == ADFFT_ERR_UNSUPPORTED_SIZE) return ADFFT_ERR_NOT_SUPPORTED;
@@ -890,6 +895,7 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
   info->passes = (p.algo == ADFFT_ALGO_FOUR_STEP) ? 2 : 1;
   info->scale = p.scale;
   info->staged = (p.algo == ADFFT_ALGO_FOLD && p.fused.args.stage_bytes > 0) ? 1 : 0;
+  info->grid = (p.algo == ADFFT_ALGO_FOLD) ? p.fused.grid_y : (p.algo == ADFFT_ALGO_FOUR_STEP) ? p.tp1.grid_y : 0;
   info->tuned = p.tuned ? 1 : 0;
   return ADFFT_OK;
 }

@@ -33,7 +33,7 @@ def main():
     ap.add_argument("--prec", type=int, default=adfft.PREC_NATIVE, help="0 native, 1 fp16x2, 2 bf16x3")
     ap.add_argument("--tune", action="store_true", help="autotune the plan first (adfft_plan_autotune)")
     ap.add_argument("--shape", default=None,
-                    help="fold launch shape fft_len,cluster,staged (adfft_plan_set_launch_shape)")
+                    help="fold launch shape fft_len,cluster,staged[,grid] (adfft_plan_set_launch_shape)")
     args = ap.parse_args()
     _build.build()
     if args.workload == "ragged_r32":
@@ -59,8 +59,7 @@ def main():
         plan.set_precision(args.prec)
     X = torch.empty((B, M), dtype=adfft.out_dtype(x.dtype), device=dev)
     if args.shape:
-        fl, cl, st = (int(v) for v in args.shape.split(","))
-        plan.set_launch_shape(fl, cl, st)
+        plan.set_launch_shape(*(int(v) for v in args.shape.split(",")))
     if args.tune:
         plan.autotune(x.data_ptr(), X.data_ptr())
     g = torch.empty_like(x) if args.adjoint else None
@@ -78,11 +77,11 @@ def main():
     ms = e0.elapsed_time(e1) / max(1, args.iters)
     info = plan.info
     nbytes = x.numel() * x.element_size() + B * M * X.element_size()
-    print("workload=%s B=%d N=%d M=%d algo=%d fft_len=%d P=%d q=%d C=%d staged=%d tuned=%d passes=%d prec=%d "
-          "adjoint=%d  "
+    print("workload=%s B=%d N=%d M=%d algo=%d fft_len=%d P=%d q=%d C=%d staged=%d grid=%d tuned=%d passes=%d "
+          "prec=%d adjoint=%d  "
           "%.4f ms/transform  %.1f GB/s (input + output bytes)  %.3e points/s"
           % (args.workload, B, N, M, info.algo, info.fft_len, info.residues, info.fold, info.cluster, info.staged,
-             info.tuned, info.passes,
+             info.grid, info.tuned, info.passes,
              args.prec, int(args.adjoint), ms, nbytes / ms / 1e6, B * M / ms * 1e3))
 
 

@@ -14,7 +14,8 @@ def lib():
 
 
 ENTRY = {"device": "NVIDIA GB300|sm_103|cuda-driver 13000", "N": 16384, "M": 131072, "batch": 4096,
-         "dtype": 0, "precision": 0, "algo": 1, "fft_len": 8192, "cluster": 4, "staged": 1, "ms": 2.33}
+         "dtype": 0, "precision": 0, "algo": 1, "fft_len": 8192, "cluster": 4, "staged": 1, "grid": 0,
+         "ms": 2.33}
 
 
 def write(path, obj):
@@ -24,7 +25,7 @@ def write(path, obj):
 
 def test_round_trip_and_merge(lib, tmp_path):
     adfft.autotune_clear()
-    e2 = dict(ENTRY, N=8192, M=20480, dtype=1, algo=3, fft_len=0, cluster=0, staged=0, ms=0.5)
+    e2 = dict(ENTRY, N=8192, M=20480, dtype=1, algo=3, fft_len=0, cluster=0, staged=0, grid=-1, ms=0.5)
     e3 = dict(ENTRY, device='other "gpu"\\x', batch=7)
     adfft.autotune_load(write(tmp_path / "a.json", {"adfft_autotune": 1, "entries": [ENTRY, e2]}))
     adfft.autotune_load(write(tmp_path / "b.json", {"adfft_autotune": 1, "entries": [e3]}))
@@ -37,7 +38,7 @@ def test_round_trip_and_merge(lib, tmp_path):
     assert len(entries) == 3
     for want in (ENTRY, e2, e3):
         e = entries[key(want)]
-        for k in ("algo", "fft_len", "cluster", "staged"):
+        for k in ("algo", "fft_len", "cluster", "staged", "grid"):
             assert e[k] == want[k], (k, e, want)
         assert abs(e["ms"] - want["ms"]) <= 1e-5 * want["ms"]
     # the saved file loads again; a later entry for the same key replaces the earlier one
@@ -64,6 +65,7 @@ def test_round_trip_and_merge(lib, tmp_path):
     '{"adfft_autotune": 1, "entries": [' + json.dumps(ENTRY) + ']} trailing',
     '{"adfft_autotune": 1, "entries": [' + json.dumps(ENTRY)[:-3] + ']}',                 # truncated
     '{"adfft_autotune": 1, "entries": [' + json.dumps(dict(ENTRY, staged=5)) + ']}',
+    '{"adfft_autotune": 1, "entries": [' + json.dumps(dict(ENTRY, grid=-2)) + ']}',
 ])
 def test_rejects_malformed_files_and_merges_nothing(lib, tmp_path, text):
     adfft.autotune_clear()
@@ -75,10 +77,20 @@ def test_rejects_malformed_files_and_merges_nothing(lib, tmp_path, text):
     assert json.loads(out.read_text())["entries"] == []
 
 
+def test_grid_field_is_optional(lib, tmp_path):
+    adfft.autotune_clear()
+    e = {k: v for k, v in ENTRY.items() if k != "grid"}
+    adfft.autotune_load(write(tmp_path / "g.json", {"adfft_autotune": 1, "entries": [e]}))
+    out = tmp_path / "out.json"
+    adfft.autotune_save(str(out))
+    assert json.loads(out.read_text())["entries"][0]["grid"] == 0
+    adfft.autotune_clear()
+
+
 def test_missing_file_and_null_arguments(lib, tmp_path):
     with pytest.raises(adfft.AdfftError):
         adfft.autotune_load(str(tmp_path / "does_not_exist.json"))
     assert lib.adfft_autotune_load(None) == -1
     assert lib.adfft_autotune_save(None) == -1
     assert lib.adfft_plan_autotune(None, None, None, None, 0) == -1
-    assert lib.adfft_plan_set_launch_shape(None, 0, 0, -1) == -1
+    assert lib.adfft_plan_set_launch_shape(None, 0, 0, -1, 0) == -1

@@ -173,19 +173,51 @@ def test_every_candidate_shape_matches_the_oracle(code, N, alpha):
     plan = adfft.Plan(N, batch=B, dtype=code, M=M)
     ran = 0
     for fft_len, cluster, staged in candidate_shapes(code, N, M):
-        try:
-            plan.set_launch_shape(fft_len, cluster, staged)
-        except adfft.AdfftError as e:
-            assert e.code == -9, (fft_len, cluster, staged, e)   # does not fit: NOT_SUPPORTED
-            continue
-        info = plan.info
-        assert (info.fft_len, info.cluster, info.staged) == (fft_len, cluster, staged)
-        X = forward(torch, plan, xt, M, dbl).cpu().numpy()
-        assert rel(X, ref) <= tol_for(M, dbl), (fft_len, cluster, staged)
-        xb = adjoint(torch, plan, gt, N, xt.dtype).cpu().numpy()
-        assert rel(xb, ref_b) <= tol_for(M, dbl), (fft_len, cluster, staged)
-        ran += 1
-    assert ran >= 4
+        for grid in (0, 1):   # resident-size grid (here one cluster per signal), and one cluster for all
+            try:
+                plan.set_launch_shape(fft_len, cluster, staged, grid)
+            except adfft.AdfftError as e:
+                assert e.code == -9, (fft_len, cluster, staged, e)   # does not fit: NOT_SUPPORTED
+                continue
+            info = plan.info
+            assert (info.fft_len, info.cluster, info.staged) == (fft_len, cluster, staged)
+            assert info.grid == (1 if grid == 1 else B)
+            X = forward(torch, plan, xt, M, dbl).cpu().numpy()
+            assert rel(X, ref) <= tol_for(M, dbl), (fft_len, cluster, staged, grid)
+            xb = adjoint(torch, plan, gt, N, xt.dtype).cpu().numpy()
+            assert rel(xb, ref_b) <= tol_for(M, dbl), (fft_len, cluster, staged, grid)
+            ran += 1
+    assert ran >= 8
+
+
+@pytest.mark.parametrize("staged", [1, 0])
+def test_grid_size_does_not_change_results(staged):
+    """Clusters loop over signals (persistent grid); every signal is transformed by
+    the same arithmetic whichever cluster takes it, so all grids agree bit for bit."""
+    torch = _torch()
+    B, N, M = 100, 16384, 131072
+    x, _ = signals.batch_r32(batch=B)
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(x).to(dev)
+    plan = adfft.Plan(N, batch=B, dtype=adfft.R32, M=M)
+    g = torch.randn((B, M), dtype=torch.complex64, device=dev)
+    outs, grads = [], []
+    for grid in (-1, 0, 1, 7):
+        plan.set_launch_shape(8192, 4, staged, grid)
+        assert plan.info.grid == {-1: B, 1: 1, 7: 7}.get(grid, plan.info.grid)
+        if grid == 0:
+            assert 1 <= plan.info.grid <= B
+        outs.append(forward(torch, plan, xt, M, False))
+        grads.append(adjoint(torch, plan, g, N, xt.dtype))
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    for o in grads[1:]:
+        assert torch.equal(o, grads[0])
+    sig = np.array([0, 37, 99])
+    bins = sample_bins(M, 400, 3)
+    got = outs[0][torch.from_numpy(sig).to(dev)][:, torch.from_numpy(bins).to(dev)].cpu().numpy()
+    ref = oracle.alpha_dft(x[sig].astype(np.float64), M, bins=bins)
+    assert rel(got, ref) <= tol_for(M, False)
 
 
 def test_autotune_forward_and_cache(tmp_path):
