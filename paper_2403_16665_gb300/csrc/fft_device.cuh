@@ -223,6 +223,13 @@ __device__ __forceinline__ float2 dsmem_ld(uint32_t addr, float2) {
   asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
   return v;
 }
+// Two adjacent float2 elements (16 bytes, 16-byte aligned address).
+__device__ __forceinline__ void dsmem_ld_pair(uint32_t addr, float2& a, float2& b) {
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y)
+               : "r"(addr)
+               : "memory");
+}
 __device__ __forceinline__ double2 dsmem_ld(uint32_t addr, double2) {
   double2 v;
   asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");

@@ -25,15 +25,24 @@ KernelFn pick_r0(int r0) {
 }
 
 // Shapes with a compile-time specialisation (all strides and pass counts constant).
-// real fp32, packed sub-FFT 8192, 8 residues, 2 per CTA, 512 threads; pad 1 per 32 (radix-32 first
-// pass writes at stride 32 without bank conflicts); 6 epilogue loads in flight per thread
-using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2, 5, 6>;
+// real fp32, packed sub-FFT 8192, 8 residues, 2 per CTA, 512 threads; padding of 2 slots per 64
+// elements (16-byte pairs stay aligned; the radix-32 first pass stores pairs without bank
+// conflicts), epilogue in pairs of k with 4 pair loads in flight per thread
+using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2, 6, 4, 2>;
+
+// the same with one residue per CTA (clusters of 8, 256 threads: two CTAs per SM)
+using ShapeR32N8192P8C8 = Shape<13, 1, 8, 256, 2, 6, 4, 2>;
+
+bool is_r32_n8192_p8(const FusedLaunch& L, int rpc, int threads) {
+  const FusedArgs& a = L.args;
+  return !L.dbl && L.mode == kLoadRealPacked && L.r0 == 32 && a.logNp == 13 && a.RPC == rpc && a.P == 8 &&
+         L.threads == threads && a.Mt == 2 * a.Mc;
+}
 
 KernelFn pick_kernel(const FusedLaunch& L) {
-  const FusedArgs& a = L.args;
-  if (!L.dbl && L.mode == kLoadRealPacked && L.r0 == 32 && a.logNp == 13 && a.RPC == 2 && a.P == 8 &&
-      L.threads == 512 && a.Mt == 2 * a.Mc)
-    return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8>;
+  if (is_r32_n8192_p8(L, 2, 512)) return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8>;
+  if (is_r32_n8192_p8(L, 1, 256))
+    return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8C8>;
   if (L.dbl) {
     switch (L.mode) {
       case kLoadComplex: return pick_r0<double2, kLoadComplex, kVptF64>(L.r0);

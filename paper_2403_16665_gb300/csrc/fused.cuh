@@ -76,14 +76,18 @@ struct FusedArgs {
 // FusedArgs at run time instead.  LOGNP: log2 of the sub-FFT length, RPC:
 // residues per CTA, P: residues per signal, T: threads per CTA, MTF: Mt / (P Np)
 // (2 for packed real input, 1 otherwise).
-// PADSH: shared-memory padding of one slot per 2^PADSH elements (0: 4, i.e. pad16);
+// PADSH, PW: shared-memory padding of PW slots per 2^PADSH elements (0: 4 and 1,
+// i.e. pad16).  With PW = 2 every even element index stays 16-byte aligned, and
+// float2 data moves in 16-byte pairs (first-pass stores, epilogue loads).
 // EU: independent epilogue loads in flight per thread (0: the generic default).
-template <int LOGNP = 0, int RPC = 0, int P = 0, int T = 0, int MTF = 0, int PADSH = 0, int EU = 0>
+template <int LOGNP = 0, int RPC = 0, int P = 0, int T = 0, int MTF = 0, int PADSH = 0, int EU = 0, int PW = 1>
 struct Shape {
   static constexpr bool fixed = LOGNP != 0 && RPC != 0 && P != 0 && T != 0 && MTF != 0;
   static constexpr int padsh = PADSH ? PADSH : 4;
+  static constexpr int pw = PW;
+  static constexpr bool pairs = PW == 2;
   static constexpr int eu = EU;
-  __device__ static __forceinline__ int pad(int p) { return p + (p >> padsh); }
+  __device__ static __forceinline__ int pad(int p) { return p + PW * (p >> padsh); }
   __device__ static __forceinline__ int logNp(const struct FusedArgs& a);
   __device__ static __forceinline__ int Np(const struct FusedArgs& a);
   __device__ static __forceinline__ int rpc(const struct FusedArgs& a);
@@ -92,30 +96,34 @@ struct Shape {
   __device__ static __forceinline__ int region(const struct FusedArgs& a);
   __device__ static __forceinline__ unsigned mt(const struct FusedArgs& a);
 };
-template <int L, int R, int PP, int TT, int F, int PS, int E>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::logNp(const FusedArgs& a) { return L ? L : a.logNp; }
-template <int L, int R, int PP, int TT, int F, int PS, int E>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::Np(const FusedArgs& a) { return L ? (1 << L) : a.Np; }
-template <int L, int R, int PP, int TT, int F, int PS, int E>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::rpc(const FusedArgs& a) { return R ? R : a.RPC; }
-template <int L, int R, int PP, int TT, int F, int PS, int E>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::p(const FusedArgs& a) { return PP ? PP : a.P; }
-template <int L, int R, int PP, int TT, int F, int PS, int E>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::threads() { return TT ? TT : (int)blockDim.x; }
-template <int L, int R, int PP, int TT, int F, int PS, int E>
-__device__ __forceinline__ int Shape<L, R, PP, TT, F, PS, E>::region(const FusedArgs& a) {
-  return L ? ((1 << L) + ((1 << L) >> (PS ? PS : 4)) + 2) : a.region;
+#define ADFFT_SHAPE_TPL template <int L, int R, int PP, int TT, int F, int PS, int E, int W>
+#define ADFFT_SHAPE Shape<L, R, PP, TT, F, PS, E, W>
+ADFFT_SHAPE_TPL
+__device__ __forceinline__ int ADFFT_SHAPE::logNp(const FusedArgs& a) { return L ? L : a.logNp; }
+ADFFT_SHAPE_TPL
+__device__ __forceinline__ int ADFFT_SHAPE::Np(const FusedArgs& a) { return L ? (1 << L) : a.Np; }
+ADFFT_SHAPE_TPL
+__device__ __forceinline__ int ADFFT_SHAPE::rpc(const FusedArgs& a) { return R ? R : a.RPC; }
+ADFFT_SHAPE_TPL
+__device__ __forceinline__ int ADFFT_SHAPE::p(const FusedArgs& a) { return PP ? PP : a.P; }
+ADFFT_SHAPE_TPL
+__device__ __forceinline__ int ADFFT_SHAPE::threads() { return TT ? TT : (int)blockDim.x; }
+ADFFT_SHAPE_TPL
+__device__ __forceinline__ int ADFFT_SHAPE::region(const FusedArgs& a) {
+  return L ? ((1 << L) + W * ((1 << L) >> (PS ? PS : 4)) + 2) : a.region;
 }
-template <int L, int R, int PP, int TT, int F, int PS, int E>
-__device__ __forceinline__ unsigned Shape<L, R, PP, TT, F, PS, E>::mt(const FusedArgs& a) {
+ADFFT_SHAPE_TPL
+__device__ __forceinline__ unsigned ADFFT_SHAPE::mt(const FusedArgs& a) {
   return (L && PP && F) ? (unsigned)(F * PP) << L : (unsigned)a.Mt;
 }
 using RuntimeShape = Shape<>;
 
 // Passes of a fixed shape: one of radix 2^LOGR0, then radix 16.
 template <class SH, int LOGR0> struct SH_PASSES;
-template <int L, int R, int PP, int TT, int F, int PS, int E, int LOGR0>
-struct SH_PASSES<Shape<L, R, PP, TT, F, PS, E>, LOGR0> { static constexpr int value = 1 + (L - LOGR0) / 4; };
+template <int L, int R, int PP, int TT, int F, int PS, int E, int W, int LOGR0>
+struct SH_PASSES<ADFFT_SHAPE, LOGR0> { static constexpr int value = 1 + (L - LOGR0) / 4; };
+#undef ADFFT_SHAPE
+#undef ADFFT_SHAPE_TPL
 
 // Shared-memory layout of the fused kernel (byte offsets).
 struct FusedSmem {
@@ -237,8 +245,15 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, co
         acc[i] = cmul(acc[i], wi);
       }
       DFT<R, V>::run(acc);
+      if constexpr (SH::pairs && (R % 2) == 0 && sizeof(V) == 8 && R <= (1 << SH::padsh)) {
+        // R outputs of one item lie in one padding block: 16-byte pair stores
+        float4* d4 = reinterpret_cast<float4*>(dst + SH::pad(j * R));
 #pragma unroll
-      for (int i = 0; i < R; ++i) dst[SH::pad(j * R + i)] = acc[i];
+        for (int i = 0; i < R; i += 2) d4[i / 2] = make_float4(acc[i].x, acc[i].y, acc[i + 1].x, acc[i + 1].y);
+      } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) dst[SH::pad(j * R + i)] = acc[i];
+      }
       e_j += d_T;
       if (e_j >= Mt) e_j -= Mt;
     }
@@ -262,9 +277,9 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
   const int region = SH::region(a);
   const bool same_j = (T & (items_res - 1)) == 0;
   const unsigned tw_step = SH::mt(a) / ((unsigned)Ns << LOGR);   // Mt / (Ns R)
-  // pad(j + i*S) = pad(j) + i*(S + S/2^padsh) for S a multiple of 2^padsh
+  // pad(j + i*S) = pad(j) + i*(S + PW S/2^padsh) for S a multiple of 2^padsh
   constexpr int PADN = 1 << SH::padsh;
-  const int in_step = items_res + (items_res >> SH::padsh);
+  const int in_step = items_res + SH::pw * (items_res >> SH::padsh);
   V v[IPT][R];
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
@@ -294,7 +309,7 @@ __device__ __forceinline__ void stockham_pass(const FusedArgs& a, V* buf, const 
 #pragma unroll
   for (int it = 0; it < IPT; ++it) DFT<R, V>::run(v[it]);
   __syncthreads();
-  const int out_step = Ns + (Ns >> SH::padsh);
+  const int out_step = Ns + SH::pw * (Ns >> SH::padsh);
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
     const int wi = threadIdx.x + it * T;
@@ -369,7 +384,9 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   const unsigned r_l = threadIdx.x % P;
   const unsigned k_step = Tp / P;
   const unsigned jtot = (MODE == kLoadRealPacked) ? (unsigned)a.Mc / 2 + 1 : (unsigned)a.Mc;
-  const unsigned per = ((jtot + a.C - 1) / a.C + P - 1) / P * P;
+  // (pair epilogue: per a multiple of 2P, so every CTA's k range starts even)
+  constexpr unsigned KG = (SH::pairs && MODE == kLoadRealPacked && sizeof(V) == 8) ? 2u : 1u;
+  const unsigned per = ((jtot + a.C - 1) / a.C + KG * P - 1) / (KG * P) * (KG * P);
   const unsigned j_first = c * per;
   const unsigned j_last = min(jtot, j_first + per) - 1;      // inclusive
   const unsigned k_first = j_first / P + threadIdx.x / P;
@@ -452,7 +469,54 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     // ---- K3: interleave epilogue through distributed shared memory
     if (a.C > 1) { cluster_arrive(); cluster_wait(); } else { __syncthreads(); }
     if (lane_ok) {
-      if (MODE == kLoadRealPacked) {
+      if constexpr (KG == 2) {
+        // pairs of k: thread (r_l, kq) handles k = 2 kq and 2 kq + 1 of residue r_l, i.e. bins
+        // j0 = 2 kq P + r_l and j1 = j0 + P; U[k], U[k+1] come in one 16-byte load, and so do
+        // the mirror values U[Np-2-k], U[Np-1-k] (residue P - r_l), except for r_l = 0
+        const unsigned Mc = (unsigned)a.Mc;
+        const unsigned half = Mc / 2;
+        const unsigned lim = min(half, j_last);
+        const unsigned Npu = (unsigned)SH::Np(a);
+        const unsigned kq_first = j_first / (2 * P) + threadIdx.x / P;
+        for (unsigned kq = kq_first; 2 * kq * P + r_l <= lim; kq += k_step * kEpilogueUnroll) {
+          V Ua[kEpilogueUnroll][2], Ub[kEpilogueUnroll][2];
+#pragma unroll
+          for (int e = 0; e < kEpilogueUnroll; ++e) {
+            const unsigned k = 2 * (kq + e * k_step);
+            if (k * P + r_l <= lim) {
+              dsmem_ld_pair(base_u + (uint32_t)SH::pad((int)k) * 8u, Ua[e][0], Ua[e][1]);
+              if (r_l != 0) {
+                // mirror of k is Np-1-k, of k+1 is Np-2-k: the pair starting at Np-2-k
+                dsmem_ld_pair(base_p + (uint32_t)SH::pad((int)(Npu - 2 - k)) * 8u, Ub[e][1], Ub[e][0]);
+              } else {
+                Ub[e][0] = dsmem_ld(base_p + (uint32_t)SH::pad((int)((Npu - k) & (Npu - 1))) * 8u, V{});
+                Ub[e][1] = dsmem_ld(base_p + (uint32_t)SH::pad((int)(Npu - 1 - k)) * 8u, V{});
+              }
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < kEpilogueUnroll; ++e) {
+            const unsigned k = 2 * (kq + e * k_step);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const unsigned j = (k + h) * P + r_l;
+              if (j <= lim) {
+                const V E = cscale(cadd(Ua[e][h], cconj(Ub[e][h])), (Rl)0.5);
+                const V O = cscale(cmul_mi(csub(Ua[e][h], cconj(Ub[e][h]))), (Rl)0.5);
+                const V wO = cmul(tab(j), O);
+                const V X1 = cscale(cadd(E, wO), S);
+                const V X2 = cscale(csub(E, wO), S);
+                st_stream(out + j, X1);
+                st_stream(out + j + Mc, X2);
+                if (j != 0 && 2 * j != Mc) {
+                  st_stream(out + (Mc - j), cconj(X2));
+                  st_stream(out + ((unsigned long long)a.M - j), cconj(X1));
+                }
+              }
+            }
+          }
+        }
+      } else if (MODE == kLoadRealPacked) {
         const unsigned Mc = (unsigned)a.Mc;
         const unsigned half = Mc / 2;
         for (unsigned kb = k_first; kb * P + r_l <= min(half, j_last); kb += k_step * kEpilogueUnroll) {

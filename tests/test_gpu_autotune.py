@@ -293,3 +293,42 @@ def test_autotune_ragged():
         got = xb[plan.in_off[i]:plan.in_off[i + 1]]
         assert (torch.linalg.norm(got - ref) / torch.linalg.norm(ref)).item() <= 2 * tol_for(M, False), (i, N, M)
     adfft.autotune_clear()
+
+
+@pytest.mark.parametrize("N,alpha,B", [(16384, 8, 6), (32768, 4, 3), (16384, 8, 45)])
+@pytest.mark.parametrize("cluster,staged", [(4, 1), (4, 0), (8, 1), (8, 0)])
+def test_specialised_sub_fft_8192_shapes(N, alpha, B, cluster, staged):
+    """Real fp32 plans whose packed sub-FFT is 8192 points with 8 residues run
+    compile-time specialised kernels (clusters of 4 with 2 residues per CTA, or of 8
+    with 1; N = 32768, alpha = 4: sub-FFT halved, fold of 2).  All bins against the
+    generic kernel (sub-FFT 4096), sampled bins against the oracle, every grid size
+    bit for bit."""
+    torch = _torch()
+    M = alpha * N
+    x = make_input(adfft.R32, B, N, 17 * N + B)
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(x).to(dev)
+    plan = adfft.Plan(N, batch=B, dtype=adfft.R32, M=M)
+    plan.set_launch_shape(4096, 4, 0, 0)   # generic kernel: 16 residues of 4096 points
+    X_ref = forward(torch, plan, xt, M, False)
+    outs = []
+    for grid in (0, -1, 1, 2):
+        try:
+            plan.set_launch_shape(8192, cluster, staged, grid)
+        except adfft.AdfftError as e:
+            assert e.code == -9 and staged == 1   # the signal does not fit next to the regions
+            pytest.skip("staging does not fit this shape")
+        info = plan.info
+        assert (info.fft_len, info.residues, info.cluster, info.staged) == (8192, 8, cluster, staged)
+        outs.append(forward(torch, plan, xt, M, False))
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    X = outs[0].cpu().numpy()
+    assert rel(X, X_ref.cpu().numpy()) <= 2 * tol_for(M, False)
+    bins = np.unique(np.concatenate([sample_bins(M, 700, N), [M // 4, M // 4 + 1, M // 2, M // 2 + 1,
+                                                               3 * M // 4, 3 * M // 4 + 1, M - 2, M - 1]]))
+    sig = np.array([0, B - 1])
+    ref = oracle.alpha_dft(x[sig].astype(np.float64), M, bins=bins)
+    assert rel(X[sig][:, bins], ref) <= tol_for(M, False)
+    m = np.arange(1, M)
+    assert np.max(np.abs(X[0][M - m] - np.conj(X[0][m]))) <= 1e-5 * np.max(np.abs(X[0]))
