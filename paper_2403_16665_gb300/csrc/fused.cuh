@@ -497,21 +497,31 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 #pragma unroll
           for (int e = 0; e < kEpilogueUnroll; ++e) {
             const unsigned k = 2 * (kq + e * k_step);
+            V X1[2], X2[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const unsigned j = (k + h) * P + r_l;
+              const V E = cscale(cadd(Ua[e][h], cconj(Ub[e][h])), (Rl)0.5);
+              const V O = cscale(cmul_mi(csub(Ua[e][h], cconj(Ub[e][h]))), (Rl)0.5);
+              const V wO = cmul(tab(j), O);
+              X1[h] = cscale(cadd(E, wO), S);
+              X2[h] = cscale(csub(E, wO), S);
               if (j <= lim) {
-                const V E = cscale(cadd(Ua[e][h], cconj(Ub[e][h])), (Rl)0.5);
-                const V O = cscale(cmul_mi(csub(Ua[e][h], cconj(Ub[e][h]))), (Rl)0.5);
-                const V wO = cmul(tab(j), O);
-                const V X1 = cscale(cadd(E, wO), S);
-                const V X2 = cscale(csub(E, wO), S);
-                st_stream(out + j, X1);
-                st_stream(out + j + Mc, X2);
-                if (j != 0 && 2 * j != Mc) {
-                  st_stream(out + (Mc - j), cconj(X2));
-                  st_stream(out + ((unsigned long long)a.M - j), cconj(X1));
-                }
+                st_stream(out + j, X1[h]);
+                st_stream(out + j + Mc, X2[h]);
+              }
+            }
+            // mirror bins: lanes of residue 0 store their two values in the opposite order, so
+            // each warp-wide store covers whole 32-byte runs Mc - j (the runs end at multiples of P)
+            const bool sw = (r_l == 0);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const V y1 = sw ? X1[1 - h] : X1[h];   // constant indices: registers, not memory
+              const V y2 = sw ? X2[1 - h] : X2[h];
+              const unsigned j = (k + (sw ? 1 - h : h)) * P + r_l;
+              if (j <= lim && j != 0 && 2 * j != Mc) {
+                st_stream(out + (Mc - j), cconj(y2));
+                st_stream(out + ((unsigned long long)a.M - j), cconj(y1));
               }
             }
           }
