@@ -27,8 +27,8 @@ KernelFn pick_r0(int r0) {
 // Shapes with a compile-time specialisation (all strides and pass counts constant).
 // real fp32, packed sub-FFT 8192, 8 residues, 2 per CTA, 512 threads; padding of 2 slots per 32
 // elements (16-byte pairs stay aligned; the radix-32 first pass stores pairs without bank
-// conflicts in every quarter-warp), epilogue in pairs of k with 4 pair loads in flight per thread
-using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2, 5, 4, 2>;
+// conflicts in every quarter-warp), epilogue in pairs of k with 5 pair loads in flight per thread
+using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2, 5, 5, 2>;
 
 // the same with one residue per CTA (clusters of 8, 256 threads: two CTAs per SM)
 using ShapeR32N8192P8C8 = Shape<13, 1, 8, 256, 2, 5, 4, 2>;

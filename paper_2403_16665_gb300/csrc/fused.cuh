@@ -478,6 +478,8 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
         const unsigned lim = min(half, j_last);
         const unsigned Npu = (unsigned)SH::Np(a);
         const unsigned kq_first = j_first / (2 * P) + threadIdx.x / P;
+        const Rl hS = S * (Rl)0.5;
+        const V wP = tab(P);   // W_M^P
         for (unsigned kq = kq_first; 2 * kq * P + r_l <= lim; kq += k_step * kEpilogueUnroll) {
           V Ua[kEpilogueUnroll][2], Ub[kEpilogueUnroll][2];
 #pragma unroll
@@ -498,14 +500,21 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
           for (int e = 0; e < kEpilogueUnroll; ++e) {
             const unsigned k = 2 * (kq + e * k_step);
             V X1[2], X2[2];
+            // (S/2)(-i) W_M^j for j = k P + r_l, and for j + P by one product with W_M^P
+            V wn = tab(k * P + r_l);
+            wn = cmake<V>(hS * wn.y, -hS * wn.x);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const unsigned j = (k + h) * P + r_l;
-              const V E = cscale(cadd(Ua[e][h], cconj(Ub[e][h])), (Rl)0.5);
-              const V O = cscale(cmul_mi(csub(Ua[e][h], cconj(Ub[e][h]))), (Rl)0.5);
-              const V wO = cmul(tab(j), O);
-              X1[h] = cscale(cadd(E, wO), S);
-              X2[h] = cscale(csub(E, wO), S);
+              if (h == 1) wn = cmul(wn, wP);
+              // X_j = (S/2)(A + (-i) W_M^j B), X_{j+Mc} = (S/2)(A - (-i) W_M^j B),
+              // A = U_j + conj U_{Mc-j}, B = U_j - conj U_{Mc-j}
+              const V A = cadd(Ua[e][h], cconj(Ub[e][h]));
+              const V B = csub(Ua[e][h], cconj(Ub[e][h]));
+              const V t = cmul(wn, B);
+              const V hA = cscale(A, hS);
+              X1[h] = cadd(hA, t);
+              X2[h] = csub(hA, t);
               if (j <= lim) {
                 st_stream(out + j, X1[h]);
                 st_stream(out + j + Mc, X2[h]);
