@@ -58,42 +58,103 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
   for (long long sig = blockIdx.y; sig < a.batch; sig += gridDim.y) {
     const V* g = reinterpret_cast<const V*>(a.in) + ((MODE == kColumns) ? sig * a.M : sig_out_off(a, sig));
 
-    // ---- prologue: conj of the CTA's residues of the (folded) spectrum, natural order
+    // ---- prologue: conj of the (folded) spectrum into the residue regions.  The CTAs
+    // of the cluster split the bins j between them and read them coalesced (packed real
+    // input: j <= Mc/2 together with the partners j + Mc, M - j, Mc - j, which give both
+    // ub_j and ub_{Mc-j}); each value goes to the region of residue j mod P, k = j / P,
+    // in whichever CTA holds it (distributed shared memory).
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
-    const unsigned total = (unsigned)a.RPC * Np;
-    for (unsigned t0 = threadIdx.x; t0 < total; t0 += T * UNR) {
-      V val[UNR];
+    if constexpr (MODE == kColumns) {
+      const unsigned total = (unsigned)a.RPC * Np;
+      for (unsigned t0 = threadIdx.x; t0 < total; t0 += T * UNR) {
+        V val[UNR];
 #pragma unroll
-      for (int e = 0; e < UNR; ++e) {
-        const unsigned t = t0 + e * T;
-        if (t < total) {
-          const unsigned rl = t >> a.logNp, k = t & (Np - 1);
-          const unsigned j = k * P + (unsigned)(r0 + rl);
-          if (MODE == kLoadRealPacked) {
-            const unsigned long long M = (unsigned long long)a.M;
-            const V g0 = g[j];
-            const V g1 = g[j + Mc];
-            const V g2 = g[(M - j) % M];                 // g_{M-j} (g_0 for j = 0)
-            const V g3 = g[Mc - j];                      // g_{Mc-j} (g_Mc for j = 0)
-            const V h0 = cscale(cadd(g0, cconj(g2)), (Rl)0.5);  // h_j
-            const V h1 = cscale(cadd(g1, cconj(g3)), (Rl)0.5);  // h_{j+Mc}
-            const V d = cmulc(csub(h0, h1), tab(j));            // W_M^{-j} (h_j - h_{j+Mc})
-            val[e] = cadd(cadd(h0, h1), cmul_pi(d));
-          } else {
-            val[e] = g[j];
+        for (int e = 0; e < UNR; ++e) {
+          const unsigned t = t0 + e * T;
+          if (t < total) {
+            const unsigned rl = t >> a.logNp, k = t & (Np - 1);
+            val[e] = g[k * P + (unsigned)(r0 + rl)];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < UNR; ++e) {
+          const unsigned t = t0 + e * T;
+          if (t < total) {
+            const unsigned rl = t >> a.logNp, k = t & (Np - 1);
+            buf[rl * a.region + pad16((int)k)] = cconj(val[e]);
           }
         }
       }
+      __syncthreads();
+    } else {
+      const unsigned jt = (MODE == kLoadRealPacked) ? Mc / 2 + 1 : Mc;
+      const unsigned perj = (jt + (unsigned)a.C - 1) / (unsigned)a.C;
+      const unsigned ja = (unsigned)c * perj, jb = min(jt, ja + perj);
+      const unsigned RPCu = (unsigned)a.RPC;
+      // shared::cluster address of element k of residue r
+      auto slot = [&](unsigned r, unsigned k) -> uint32_t {
+        const unsigned owner = fdiv(r, a.divRPC);
+        return dsmem_addr(buf + (r - owner * RPCu) * a.region + pad16((int)k), owner);
+      };
+      // bins per thread and pass (loads in flight, bounded by registers)
+      constexpr int UP = (MODE == kLoadRealPacked) ? (sizeof(V) == 16 ? 1 : 2) : UNR;
+      for (unsigned j0 = ja + threadIdx.x; j0 < jb; j0 += T * UP) {
+        if constexpr (MODE == kLoadRealPacked) {
+          const unsigned long long M = (unsigned long long)a.M;
+          V g0[UP], g1[UP], g2[UP], g3[UP];
 #pragma unroll
-      for (int e = 0; e < UNR; ++e) {
-        const unsigned t = t0 + e * T;
-        if (t < total) {
-          const unsigned rl = t >> a.logNp, k = t & (Np - 1);
-          buf[rl * a.region + pad16((int)k)] = cconj(val[e]);
+          for (int e = 0; e < UP; ++e) {
+            const unsigned j = j0 + e * T;
+            if (j < jb) {
+              g0[e] = g[j];
+              g1[e] = g[j + Mc];
+              g2[e] = g[(M - j) % M];   // g_{M-j} (g_0 for j = 0)
+              g3[e] = g[Mc - j];        // g_{Mc-j} (g_Mc for j = 0)
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < UP; ++e) {
+            const unsigned j = j0 + e * T;
+            if (j < jb) {
+              // ub_j = (h_j + h_{j+Mc}) + i W_M^{-j} (h_j - h_{j+Mc}), h_m = (g_m + conj g_{M-m}) / 2
+              {
+                const V h0 = cscale(cadd(g0[e], cconj(g2[e])), (Rl)0.5);
+                const V h1 = cscale(cadd(g1[e], cconj(g3[e])), (Rl)0.5);
+                const V d = cmulc(csub(h0, h1), tab(j));
+                const unsigned q = fdiv(j, a.divP);
+                dsmem_st(slot(j - q * P, q), cconj(cadd(cadd(h0, h1), cmul_pi(d))));
+              }
+              if (j != 0 && 2 * j != Mc) {
+                // ub_{Mc-j}: the same four bins in the roles (g_{Mc-j}, g_{M-j}, g_{j+Mc}, g_j)
+                const unsigned jm = Mc - j;
+                const V h0 = cscale(cadd(g3[e], cconj(g1[e])), (Rl)0.5);
+                const V h1 = cscale(cadd(g2[e], cconj(g0[e])), (Rl)0.5);
+                const V d = cmulc(csub(h0, h1), tab(jm));
+                const unsigned q = fdiv(jm, a.divP);
+                dsmem_st(slot(jm - q * P, q), cconj(cadd(cadd(h0, h1), cmul_pi(d))));
+              }
+            }
+          }
+        } else {
+          V v[UP];
+#pragma unroll
+          for (int e = 0; e < UP; ++e) {
+            const unsigned j = j0 + e * T;
+            if (j < jb) v[e] = g[j];
+          }
+#pragma unroll
+          for (int e = 0; e < UP; ++e) {
+            const unsigned j = j0 + e * T;
+            if (j < jb) {
+              const unsigned q = fdiv(j, a.divP);
+              dsmem_st(slot(j - q * P, q), cconj(v[e]));
+            }
+          }
         }
       }
+      // every CTA's stores have landed before the transforms read them
+      if (a.C > 1) { cluster_arrive(); cluster_wait(); } else { __syncthreads(); }
     }
-    __syncthreads();
 
     // ---- inverse FFTs: forward Stockham passes on the conjugated data
     {
@@ -110,37 +171,67 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
       }
     }
 
-    // ---- reduction over residues for this CTA's range of n
+    // ---- reduction over residues for this CTA's range of n: the P residue values of an n
+    // are loaded in groups of 8 (fp64: 2), all in flight, before they are summed
     if (a.C > 1) { cluster_arrive(); cluster_wait(); } else { __syncthreads(); }
-    for (unsigned n = n0 + threadIdx.x; n < n1; n += T) {
-      const unsigned np = n & (Np - 1);
-      // conj(W_Mc^{r n}) = conj(W_Mt^{s r n}); w = W_Mt^{s n}, powers by products
-      const unsigned e1 = (unsigned)(((unsigned long long)s * n) % Mt);
-      const V w = tab(e1);
-      V wr = cmake<V>(1, 0);
-      V acc = czero<V>();
-      for (unsigned r = 0; r < P; ++r) {
-        const unsigned owner = r / (unsigned)a.RPC, rl = r - owner * (unsigned)a.RPC;
-        const V* src = buf + rl * a.region + pad16((int)np);
-        const V y = (a.C > 1) ? *cluster.map_shared_rank(src, owner) : *src;
-        // the buffer holds FFT(conj .) = conj(IFFT(.)): IFFT value = conj(y)
-        acc = cadd(acc, cmulc(cconj(y), wr));
-        if ((r & 7u) == 7u) {
-          // re-anchor the power chain every 8 steps on an exact table entry
-          wr = tab((unsigned)(((unsigned long long)s * (r + 1) * n) % Mt));
-        } else {
-          wr = cmul(wr, w);
+    {
+      const unsigned RPCu = (unsigned)a.RPC;
+      constexpr int G = sizeof(V) == 16 ? 2 : 8;    // residue values in flight per n
+      constexpr int NH = 1;                          // values of n per thread
+      for (unsigned nb = n0 + threadIdx.x; nb < n1; nb += NH * T) {
+        V acc[NH], w[NH], wr[NH];
+        unsigned nn[NH];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+          acc[h] = czero<V>();
+          nn[h] = nb + h * T;
+          // conj(W_Mc^{r n}) = conj(W_Mt^{s r n}); w = W_Mt^{s n}, powers by products
+          w[h] = tab((unsigned)(((unsigned long long)s * min(nn[h], n1 - 1)) % Mt));
         }
-      }
-      acc = cscale(acc, S);
-      unsigned char* obase = reinterpret_cast<unsigned char*>(a.out);
-      if (MODE == kLoadRealPlain) {
-        reinterpret_cast<Rl*>(obase + sig_in_bytes(a, sig))[n] = acc.x;
-      } else if (MODE == kColumns) {
-        // transpose of the two-pass first pass: column (sig mod cols) of the core, stride cols
-        reinterpret_cast<V*>(obase + sig_in_bytes(a, sig / a.cols))[(sig % a.cols) + (long long)n * a.cols] = acc;
-      } else {
-        reinterpret_cast<V*>(obase + sig_in_bytes(a, sig))[n] = acc;
+        for (unsigned rb = 0; rb < P; rb += G) {
+          V y[NH][G];
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            const unsigned np = nn[h] & (Np - 1);
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+              const unsigned r = rb + u;
+              if (r < P && nn[h] < n1) {
+                const unsigned owner = fdiv(r, a.divRPC);
+                const V* src = buf + (r - owner * RPCu) * a.region + pad16((int)np);
+                y[h][u] = (a.C > 1) ? dsmem_ld(dsmem_addr(src, owner), V{}) : *src;
+              }
+            }
+          }
+#pragma unroll
+          for (int h = 0; h < NH; ++h) {
+            // anchor the power chain on an exact table entry at the start of each group
+            wr[h] = tab((unsigned)(((unsigned long long)s * rb * min(nn[h], n1 - 1)) % Mt));
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+              if (rb + u < P) {
+                // the buffer holds FFT(conj .) = conj(IFFT(.)): IFFT value = conj(y)
+                acc[h] = cadd(acc[h], cmulc(cconj(y[h][u]), wr[h]));
+                wr[h] = cmul(wr[h], w[h]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+          const unsigned n = nn[h];
+          if (n >= n1) continue;
+          const V v = cscale(acc[h], S);
+          unsigned char* obase = reinterpret_cast<unsigned char*>(a.out);
+          if (MODE == kLoadRealPlain) {
+            reinterpret_cast<Rl*>(obase + sig_in_bytes(a, sig))[n] = v.x;
+          } else if (MODE == kColumns) {
+            // transpose of the two-pass first pass: column (sig mod cols) of the core, stride cols
+            reinterpret_cast<V*>(obase + sig_in_bytes(a, sig / a.cols))[(sig % a.cols) + (long long)n * a.cols] = v;
+          } else {
+            reinterpret_cast<V*>(obase + sig_in_bytes(a, sig))[n] = v;
+          }
+        }
       }
     }
     if (a.C > 1) cluster_arrive_relaxed(); else __syncthreads();
