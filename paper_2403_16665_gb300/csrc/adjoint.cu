@@ -22,7 +22,15 @@ KernelFn pick_r0(int r0) {
   }
 }
 
+// compile-time shape of the 4096 x 16384, alpha = 8 class (packed sub-FFT 8192, 8 residues,
+// 2 per CTA, 512 threads, padding of 2 slots per 32 elements), as in the forward kernel
+using AdjShapeR32N8192P8 = Shape<13, 2, 8, 512, 2, 5, 0, 2>;
+
 KernelFn pick_kernel(const FusedLaunch& L) {
+  const FusedArgs& a = L.args;
+  if (!L.dbl && L.mode == kLoadRealPacked && L.r0 == 32 && a.logNp == 13 && a.RPC == 2 && a.P == 8 &&
+      L.threads == 512 && a.Mt == 2 * a.Mc)
+    return adjoint_kernel<float2, kLoadRealPacked, 32, 32, AdjShapeR32N8192P8>;
   const int vpt = fused_values_per_thread(L.dbl);
   if (L.dbl) {
     (void)vpt;

@@ -23,27 +23,28 @@
 
 namespace adfft {
 
-template <typename V, int MODE, int VPT, int R0>
+// SH: compile-time shape (as for the forward kernel), or RuntimeShape.
+template <typename V, int MODE, int VPT, int R0, class SH = RuntimeShape>
 __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
   using Rl = typename real_of<V>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int esz = (int)sizeof(V);
   const int tw_n = a.tw_lo_n + a.tw_hi_n;
-  const FusedSmem L = fused_smem_layout(tw_n, 0, a.RPC, a.region, esz);
+  const int region = SH::region(a);
+  const FusedSmem L = fused_smem_layout(tw_n, 0, SH::rpc(a), region, esz);
   V* tw_s = reinterpret_cast<V*>(smem_raw + L.tw);
   V* buf = reinterpret_cast<V*>(smem_raw + L.buf);
   for (int i = threadIdx.x; i < tw_n; i += blockDim.x) tw_s[i] = reinterpret_cast<const V*>(a.tw)[i];
   __syncthreads();
   TwTable<V> tab{tw_s, tw_s + a.tw_lo_n, a.tw_bits, (1u << a.tw_bits) - 1u};
 
-  cg::cluster_group cluster = cg::this_cluster();
   const int c = (int)blockIdx.x;
-  const int r0 = c * a.RPC;
-  const unsigned T = blockDim.x;
-  const unsigned P = (unsigned)a.P;
-  const unsigned Np = (unsigned)a.Np;
+  const int r0 = c * SH::rpc(a);
+  const unsigned T = (unsigned)SH::threads();
+  const unsigned P = (unsigned)SH::p(a);
+  const unsigned Np = (unsigned)SH::Np(a);
   const unsigned Mc = (unsigned)a.Mc;
-  const unsigned Mt = (unsigned)a.Mt;
+  const unsigned Mt = SH::mt(a);
   const unsigned s = Mt / Mc;
   const Rl S = (Rl)a.scale;
   constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : R0 == 16 ? 4 : 5;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
     // in whichever CTA holds it (distributed shared memory).
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
     if constexpr (MODE == kColumns) {
-      const unsigned total = (unsigned)a.RPC * Np;
+      const unsigned total = (unsigned)SH::rpc(a) * Np;
       for (unsigned t0 = threadIdx.x; t0 < total; t0 += T * UNR) {
         V val[UNR];
 #pragma unroll
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
           const unsigned t = t0 + e * T;
           if (t < total) {
             const unsigned rl = t >> a.logNp, k = t & (Np - 1);
-            buf[rl * a.region + pad16((int)k)] = cconj(val[e]);
+            buf[rl * region + SH::pad((int)k)] = cconj(val[e]);
           }
         }
       }
@@ -90,11 +91,11 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
       const unsigned jt = (MODE == kLoadRealPacked) ? Mc / 2 + 1 : Mc;
       const unsigned perj = (jt + (unsigned)a.C - 1) / (unsigned)a.C;
       const unsigned ja = (unsigned)c * perj, jb = min(jt, ja + perj);
-      const unsigned RPCu = (unsigned)a.RPC;
+      const unsigned RPCu = (unsigned)SH::rpc(a);
       // shared::cluster address of element k of residue r
       auto slot = [&](unsigned r, unsigned k) -> uint32_t {
-        const unsigned owner = fdiv(r, a.divRPC);
-        return dsmem_addr(buf + (r - owner * RPCu) * a.region + pad16((int)k), owner);
+        const unsigned owner = SH::fixed ? r / RPCu : fdiv(r, a.divRPC);
+        return dsmem_addr(buf + (r - owner * RPCu) * region + SH::pad((int)k), owner);
       };
       // bins per thread and pass (loads in flight, bounded by registers)
       constexpr int UP = (MODE == kLoadRealPacked) ? (sizeof(V) == 16 ? 1 : 2) : UNR;
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
                 const V h0 = cscale(cadd(g0[e], cconj(g2[e])), (Rl)0.5);
                 const V h1 = cscale(cadd(g1[e], cconj(g3[e])), (Rl)0.5);
                 const V d = cmulc(csub(h0, h1), tab(j));
-                const unsigned q = fdiv(j, a.divP);
+                const unsigned q = SH::fixed ? j / P : fdiv(j, a.divP);
                 dsmem_st(slot(j - q * P, q), cconj(cadd(cadd(h0, h1), cmul_pi(d))));
               }
               if (j != 0 && 2 * j != Mc) {
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
                 const V h0 = cscale(cadd(g3[e], cconj(g1[e])), (Rl)0.5);
                 const V h1 = cscale(cadd(g2[e], cconj(g0[e])), (Rl)0.5);
                 const V d = cmulc(csub(h0, h1), tab(jm));
-                const unsigned q = fdiv(jm, a.divP);
+                const unsigned q = SH::fixed ? jm / P : fdiv(jm, a.divP);
                 dsmem_st(slot(jm - q * P, q), cconj(cadd(cadd(h0, h1), cmul_pi(d))));
               }
             }
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
           for (int e = 0; e < UP; ++e) {
             const unsigned j = j0 + e * T;
             if (j < jb) {
-              const unsigned q = fdiv(j, a.divP);
+              const unsigned q = SH::fixed ? j / P : fdiv(j, a.divP);
               dsmem_st(slot(j - q * P, q), cconj(v[e]));
             }
           }
@@ -160,14 +161,23 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
     {
       int Ns = 1, logNs = 0;
       if constexpr (R0 > 1) {
-        stockham_pass<R0, VPT, V>(a, buf, tab, Ns, logNs);
+        stockham_pass<R0, VPT, V, SH>(a, buf, tab, Ns, logNs);
         Ns = R0;
         logNs = LOGR0;
       }
-      for (int p = 1; p < a.nrad; ++p) {
-        stockham_pass<16, VPT, V>(a, buf, tab, Ns, logNs);
-        Ns <<= 4;
-        logNs += 4;
+      if constexpr (SH::fixed) {
+#pragma unroll
+        for (int p = 1; p < SH_PASSES<SH, LOGR0>::value; ++p) {
+          stockham_pass<16, VPT, V, SH>(a, buf, tab, Ns, logNs);
+          Ns <<= 4;
+          logNs += 4;
+        }
+      } else {
+        for (int p = 1; p < a.nrad; ++p) {
+          stockham_pass<16, VPT, V, SH>(a, buf, tab, Ns, logNs);
+          Ns <<= 4;
+          logNs += 4;
+        }
       }
     }
 
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
     // are loaded in groups of 8 (fp64: 2), all in flight, before they are summed
     if (a.C > 1) { cluster_arrive(); cluster_wait(); } else { __syncthreads(); }
     {
-      const unsigned RPCu = (unsigned)a.RPC;
+      const unsigned RPCu = (unsigned)SH::rpc(a);
       constexpr int G = sizeof(V) == 16 ? 2 : 8;    // residue values in flight per n
       constexpr int NH = 1;                          // values of n per thread
       for (unsigned nb = n0 + threadIdx.x; nb < n1; nb += NH * T) {
@@ -197,8 +207,8 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
             for (int u = 0; u < G; ++u) {
               const unsigned r = rb + u;
               if (r < P && nn[h] < n1) {
-                const unsigned owner = fdiv(r, a.divRPC);
-                const V* src = buf + (r - owner * RPCu) * a.region + pad16((int)np);
+                const unsigned owner = SH::fixed ? r / RPCu : fdiv(r, a.divRPC);
+                const V* src = buf + (r - owner * RPCu) * region + SH::pad((int)np);
                 y[h][u] = (a.C > 1) ? dsmem_ld(dsmem_addr(src, owner), V{}) : *src;
               }
             }
