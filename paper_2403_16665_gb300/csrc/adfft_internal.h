@@ -123,6 +123,12 @@ struct Plan {
   size_t out_bytes() const { return (size_t)batch * (size_t)M * out_elem; }
 };
 
+// Compile-time-shape kernels of the real classes with a 16384-point packed sub-FFT and one
+// residue per CTA (spec16k.cu); nullptr when the launch is not of that class.
+using SpecKernel = void (*)(const FusedArgs);
+SpecKernel spec16k_forward(const FusedLaunch& L);
+SpecKernel spec16k_adjoint(const FusedLaunch& L);
+
 // Kernel launchers (fused.cu).  Return a cudaError_t.
 cudaError_t fused_prepare(const FusedLaunch& L);   // sets function attributes once
 cudaError_t fused_launch(const FusedLaunch& L, const void* in, void* out, cudaStream_t stream);

@@ -31,6 +31,7 @@ KernelFn pick_kernel(const FusedLaunch& L) {
   if (!L.dbl && L.mode == kLoadRealPacked && L.r0 == 32 && a.logNp == 13 && a.RPC == 2 && a.P == 8 &&
       L.threads == 512 && a.Mt == 2 * a.Mc)
     return adjoint_kernel<float2, kLoadRealPacked, 32, 32, AdjShapeR32N8192P8>;
+  if (KernelFn k = spec16k_adjoint(L)) return k;
   const int vpt = fused_values_per_thread(L.dbl);
   if (L.dbl) {
     (void)vpt;

@@ -41,6 +41,7 @@ bool is_r32_n8192_p8(const FusedLaunch& L, int rpc, int threads) {
 
 KernelFn pick_kernel(const FusedLaunch& L) {
   if (is_r32_n8192_p8(L, 2, 512)) return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8>;
+  if (KernelFn k = spec16k_forward(L)) return k;
   if (is_r32_n8192_p8(L, 1, 256))
     return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8C8>;
   if (L.dbl) {

@@ -65,6 +65,7 @@ def rel(a, b):
 @pytest.mark.parametrize("code,N,alpha,fft_len,cluster", [
     (adfft.R32, 1 << 16, 2, 16384, 4), (adfft.R32, 1 << 16, 3, 16384, 6), (adfft.R32, 1 << 16, 4, 16384, 8),
     (adfft.R32, 1 << 16, 8, 16384, 16), (adfft.C64, 1 << 15, 2, 16384, 4), (adfft.R64, 1 << 15, 4, 8192, 8),
+    (adfft.R32, 1 << 16, 2.5, 16384, 5), (adfft.R32, 1 << 15, 8, 16384, 8), (adfft.R32, 1 << 15, 3, 16384, 3),
 ])
 def test_halved_sub_fft_single_pass(code, N, alpha, fft_len, cluster):
     torch = _torch()
