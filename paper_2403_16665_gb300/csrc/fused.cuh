@@ -215,6 +215,54 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, co
   const unsigned s = SH::fixed ? Mt / ((unsigned)SH::p(a) << SH::logNp(a)) : (unsigned)(a.Mt / a.Mc);
   const int rpc = SH::rpc(a);
   const int region = SH::region(a);
+  // one item: elements j + i items (+ f Np) of residue r0 + rl -> R outputs at j R .. j R + R - 1
+  auto item = [&](int rl, int j, const V& c1, const V& g1, unsigned e_j) {
+    V* dst = buf + rl * region;
+    V acc[R];
+    // fold: acc[i] = sum_f u[j + i items + f Np] g^f
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = ld_any<V, STAGED>(a, u, su, j + i * items, mode);
+    if (a.q > 1) {
+      V gf = g1;
+      for (int f = 1; f < a.q; ++f) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_any<V, STAGED>(a, u, su, j + i * items + f * Np, mode), gf));
+        gf = cmul(gf, g1);
+      }
+    }
+    // residue twiddle W^{s r j} c^i
+    V wi = tab(e_j);
+    acc[0] = cmul(acc[0], wi);
+#pragma unroll
+    for (int i = 1; i < R; ++i) {
+      wi = cmul(wi, c1);
+      acc[i] = cmul(acc[i], wi);
+    }
+    DFT<R, V>::run(acc);
+    if constexpr (SH::pairs && (R % 2) == 0 && sizeof(V) == 8 && R <= (1 << SH::padsh)) {
+      // R outputs of one item lie in one padding block: 16-byte pair stores
+      float4* d4 = reinterpret_cast<float4*>(dst + SH::pad(j * R));
+#pragma unroll
+      for (int i = 0; i < R; i += 2) d4[i / 2] = make_float4(acc[i].x, acc[i].y, acc[i + 1].x, acc[i + 1].y);
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; ++i) dst[SH::pad(j * R + i)] = acc[i];
+    }
+  };
+  if (items < (int)T) {
+    // fewer items per residue than threads: the threads take (residue, item) pairs of all
+    // the CTA's residues at once, so that none idles while the residues are done in turn
+    const int log_items = SH::logNp(a) - (R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5);
+#pragma unroll 1
+    for (int t = threadIdx.x; t < rpc * items; t += T) {
+      const int rl = t >> log_items, j = t & (items - 1);
+      const unsigned long long sr = (unsigned long long)s * (unsigned)(r0 + rl);
+      const V c1 = tab((unsigned)((sr * (unsigned)items) % Mt));
+      const V g1 = tab((unsigned)((sr * (unsigned)Np) % Mt));
+      item(rl, j, c1, g1, (unsigned)((sr * (unsigned)j) % Mt));
+    }
+    return;
+  }
 #pragma unroll 1
   for (int rl = 0; rl < rpc; ++rl) {
     const unsigned long long sr = (unsigned long long)s * (unsigned)(r0 + rl);
@@ -222,38 +270,8 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, co
     const V g1 = tab((unsigned)((sr * (unsigned)Np) % Mt));
     const unsigned d_T = (unsigned)((sr * T) % Mt);
     unsigned e_j = (unsigned)((sr * threadIdx.x) % Mt);
-    V* dst = buf + rl * region;
     for (int j = threadIdx.x; j < items; j += T) {
-      V acc[R];
-      // fold: acc[i] = sum_f u[j + i items + f Np] g^f
-#pragma unroll
-      for (int i = 0; i < R; ++i) acc[i] = ld_any<V, STAGED>(a, u, su, j + i * items, mode);
-      if (a.q > 1) {
-        V gf = g1;
-        for (int f = 1; f < a.q; ++f) {
-#pragma unroll
-          for (int i = 0; i < R; ++i) acc[i] = cadd(acc[i], cmul(ld_any<V, STAGED>(a, u, su, j + i * items + f * Np, mode), gf));
-          gf = cmul(gf, g1);
-        }
-      }
-      // residue twiddle W^{s r j} c^i
-      V wi = tab(e_j);
-      acc[0] = cmul(acc[0], wi);
-#pragma unroll
-      for (int i = 1; i < R; ++i) {
-        wi = cmul(wi, c1);
-        acc[i] = cmul(acc[i], wi);
-      }
-      DFT<R, V>::run(acc);
-      if constexpr (SH::pairs && (R % 2) == 0 && sizeof(V) == 8 && R <= (1 << SH::padsh)) {
-        // R outputs of one item lie in one padding block: 16-byte pair stores
-        float4* d4 = reinterpret_cast<float4*>(dst + SH::pad(j * R));
-#pragma unroll
-        for (int i = 0; i < R; i += 2) d4[i / 2] = make_float4(acc[i].x, acc[i].y, acc[i + 1].x, acc[i + 1].y);
-      } else {
-#pragma unroll
-        for (int i = 0; i < R; ++i) dst[SH::pad(j * R + i)] = acc[i];
-      }
+      item(rl, j, c1, g1, e_j);
       e_j += d_T;
       if (e_j >= Mt) e_j -= Mt;
     }
