@@ -589,6 +589,16 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
           }
         }
       } else {
+        // kColumns: row twiddle W_Mpost^{m col}; along a thread's bins m steps by k_step P, so
+        // the twiddle steps by one product with W_Mpost^{k_step P col}, re-anchored on the
+        // table at every group of kEpilogueUnroll bins
+        const V* plo = reinterpret_cast<const V*>(a.post_tw);
+        const V* phi = plo + a.post_lo_n;
+        const unsigned long long pmask = (1ull << a.post_bits) - 1;
+        auto post_tab = [&](unsigned long long e2) { return cmul(__ldg(phi + (e2 >> a.post_bits)), __ldg(plo + (e2 & pmask))); };
+        V pstep = czero<V>();
+        if (MODE == kColumns)
+          pstep = post_tab(((unsigned long long)k_step * P * col) % (unsigned long long)a.Mpost);
         for (unsigned kb = k_first; kb * P + r_l <= j_last; kb += k_step * kEpilogueUnroll) {
           V Ua[kEpilogueUnroll];
 #pragma unroll
@@ -596,6 +606,9 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
             const unsigned k = kb + e * k_step;
             if (k * P + r_l <= j_last) Ua[e] = dsmem_ld(base_u + (uint32_t)SH::pad((int)k) * (uint32_t)sizeof(V), V{});
           }
+          V pw = czero<V>();
+          if (MODE == kColumns)
+            pw = post_tab(((unsigned long long)(kb * P + r_l) * col) % (unsigned long long)a.Mpost);
 #pragma unroll
           for (int e = 0; e < kEpilogueUnroll; ++e) {
             const unsigned k = kb + e * k_step;
@@ -603,11 +616,8 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
             if (m <= j_last) {
               V y = cscale(Ua[e], S);
               if (MODE == kColumns) {
-                // row twiddle W_Mpost^{m col}
-                const unsigned long long e2 = ((unsigned long long)m * col) % (unsigned long long)a.Mpost;
-                const V* lo = reinterpret_cast<const V*>(a.post_tw);
-                const V* hi = lo + a.post_lo_n;
-                y = cmul(y, cmul(__ldg(hi + (e2 >> a.post_bits)), __ldg(lo + (e2 & ((1ull << a.post_bits) - 1)))));
+                y = cmul(y, pw);
+                pw = cmul(pw, pstep);
               }
               st_stream(out + m, y);
             }

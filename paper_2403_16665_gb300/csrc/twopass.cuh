@@ -67,16 +67,27 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
     const V* src = reinterpret_cast<const V*>(t.scratch) + (size_t)sig * B * R1;
     // columns 0..W-1: m1 = p0 + w;  W..2W-1: the mirrors (R1 - m1) mod R1
     const unsigned ncol = t.real_packed ? 2 * W : W;
-    for (unsigned idx = threadIdx.x; idx < ncol * B; idx += T) {
-      const unsigned w = idx % ncol, b = idx / ncol;   // consecutive threads: consecutive columns
-      V v = czero<V>();
-      const unsigned pw = (w < W) ? w : w - W;
-      if (pw < np) {
-        const unsigned long long m1 = p0 + pw;
-        const unsigned long long col = (w < W) ? m1 : (R1 - m1) % R1;
-        v = __ldg(src + (size_t)b * R1 + col);
+    // (8 loads in flight per thread before the shared-memory stores)
+    constexpr int UL = 8;
+    for (unsigned i0 = threadIdx.x; i0 < ncol * B; i0 += T * UL) {
+      V v[UL];
+#pragma unroll
+      for (int e = 0; e < UL; ++e) {
+        const unsigned idx = i0 + e * T;
+        const unsigned w = idx % ncol, b = idx / ncol;   // consecutive threads: consecutive columns
+        v[e] = czero<V>();
+        const unsigned pw = (w < W) ? w : w - W;
+        if (idx < ncol * B && pw < np) {
+          const unsigned long long m1 = p0 + pw;
+          const unsigned long long col = (w < W) ? m1 : (R1 - m1) % R1;
+          v[e] = __ldg(src + (size_t)b * R1 + col);
+        }
       }
-      buf[w * a.region + pad16((int)b)] = v;
+#pragma unroll
+      for (int e = 0; e < UL; ++e) {
+        const unsigned idx = i0 + e * T;
+        if (idx < ncol * B) buf[(idx % ncol) * a.region + pad16((int)(idx / ncol))] = v[e];
+      }
     }
     __syncthreads();
     {
@@ -166,25 +177,43 @@ __global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoP
 
   for (long long sig = blockIdx.y; sig < t.batch; sig += gridDim.y) {
     const V* g = reinterpret_cast<const V*>(t.out) + (t.f.offs ? t.f.offs[2 * sig + 1] : sig * t.M);
-    for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
-      const unsigned w = idx % W, m2 = idx / W;
-      V v = czero<V>();
-      if (w < np) {
-        const unsigned long long j = p0 + w + R1 * m2;
-        if (t.real_packed) {
-          const V g0 = __ldg(g + j);
-          const V g1 = __ldg(g + j + Mc);
-          const V g2 = __ldg(g + (M - j) % M);
-          const V g3 = __ldg(g + (Mc - j));
-          const V h0 = cscale(cadd(g0, cconj(g2)), (Rl)0.5);
-          const V h1 = cscale(cadd(g1, cconj(g3)), (Rl)0.5);
-          const V d = cmulc(csub(h0, h1), tw_global<V>(t.wM, t.wM_lo_n, t.wM_bits, j));
-          v = cadd(cadd(h0, h1), cmul_pi(d));
-        } else {
-          v = __ldg(g + j);
+    // (UA elements' loads in flight per thread before they are combined and stored)
+    constexpr int UA = sizeof(V) == 16 ? 1 : 2;
+    for (unsigned i0 = threadIdx.x; i0 < W * B; i0 += T * UA) {
+      V g0[UA], g1[UA], g2[UA], g3[UA];
+#pragma unroll
+      for (int e = 0; e < UA; ++e) {
+        const unsigned idx = i0 + e * T;
+        const unsigned w = idx % W, m2 = idx / W;
+        if (idx < W * B && w < np) {
+          const unsigned long long j = p0 + w + R1 * m2;
+          g0[e] = __ldg(g + j);
+          if (t.real_packed) {
+            g1[e] = __ldg(g + j + Mc);
+            g2[e] = __ldg(g + (M - j) % M);
+            g3[e] = __ldg(g + (Mc - j));
+          }
         }
       }
-      buf[w * a.region + pad16((int)m2)] = cconj(v);
+#pragma unroll
+      for (int e = 0; e < UA; ++e) {
+        const unsigned idx = i0 + e * T;
+        if (idx >= W * B) continue;
+        const unsigned w = idx % W, m2 = idx / W;
+        V v = czero<V>();
+        if (w < np) {
+          const unsigned long long j = p0 + w + R1 * m2;
+          if (t.real_packed) {
+            const V h0 = cscale(cadd(g0[e], cconj(g2[e])), (Rl)0.5);
+            const V h1 = cscale(cadd(g1[e], cconj(g3[e])), (Rl)0.5);
+            const V d = cmulc(csub(h0, h1), tw_global<V>(t.wM, t.wM_lo_n, t.wM_bits, j));
+            v = cadd(cadd(h0, h1), cmul_pi(d));
+          } else {
+            v = g0[e];
+          }
+        }
+        buf[w * a.region + pad16((int)m2)] = cconj(v);
+      }
     }
     __syncthreads();
     {
