@@ -106,7 +106,7 @@ typedef struct {
     int32_t tuned;        /* 1 if the launch shape came from the autotuner or its cache
                              (ragged plans: every shape class) */
     int32_t grid;         /* clusters the (first) kernel launches; each loops over signals */
-    int32_t reserved;
+    int32_t four_step_a;  /* four-step form: length A of the pass-1 transforms (fft_len = A*B) */
 } adfft_plan_info_t;
 
 /*
@@ -214,7 +214,8 @@ int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *s
  *
  * adfft_plan_autotune times the forward transform of the plan for every
  * candidate launch shape (sub-FFT length, cluster size, input staging, a
- * resident-size or one-per-signal grid; the two-pass form where it applies) with `iters` timed launches each (1..100;
+ * resident-size or one-per-signal grid; the two-pass form, with every split
+ * of its transform length into A*B, where it applies) with `iters` timed launches each (1..100;
  * 0 means 3) on the caller's buffers, keeps the fastest, and records it in
  * the process-wide tuning cache under (GPU name, driver version, N, M, batch,
  * dtype, precision).  d_in and d_out are as for adfft_execute (d_out is

@@ -50,7 +50,7 @@ class PlanInfo(ctypes.Structure):
                 ("dtype", ctypes.c_int32), ("algo", ctypes.c_int32), ("fft_len", ctypes.c_int64),
                 ("residues", ctypes.c_int64), ("fold", ctypes.c_int64), ("cluster", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("scale", ctypes.c_double), ("staged", ctypes.c_int32),
-                ("tuned", ctypes.c_int32), ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tuned", ctypes.c_int32), ("grid", ctypes.c_int32), ("four_step_a", ctypes.c_int32)]
 
 
 _lib = None

@@ -91,6 +91,7 @@ struct Plan {
   // two-pass path (sub-FFT beyond one cluster): pass 1 = fused kColumns launch, pass 2 = columns
   bool tp_ok = false;
   int64_t tp_A = 0, tp_B = 0;
+  int64_t tp_force_A = 0;             // two-pass split chosen by the autotuner (0: the default rule)
   FusedLaunch tp1{};
   TwoPassLaunch tp2{};
   void* d_tp_tw1 = nullptr;           // pass-1 W_R1 table

@@ -40,6 +40,7 @@ struct Key {
 struct Entry {
   int algo = ADFFT_ALGO_FOLD;   // ADFFT_ALGO_FOLD or ADFFT_ALGO_FOUR_STEP
   FoldChoice fold{};
+  int64_t tp_a = 0;             // four-step: length A of the pass-1 transforms (0: default rule)
   double ms = 0.0;              // time per forward transform when tuned
 };
 
@@ -77,6 +78,8 @@ Key key_of(const Plan& p, const std::string& dev) {
 // Apply an entry to a plan; on failure the plan keeps its current shape.
 int apply(Plan& p, const Entry& e) {
   if (e.algo == ADFFT_ALGO_FOUR_STEP) {
+    if (p.tp_ok && p.tp_A != e.tp_a && e.tp_a > 0) release_twopass(p);
+    p.tp_force_A = e.tp_a;
     int rc = setup_twopass(p);
     if (rc == ADFFT_OK) rc = prepare_precision(p);
     if (rc != ADFFT_OK) return rc;
@@ -135,7 +138,8 @@ int tune_uniform(Plan& p, const void* in, void* out, cudaStream_t s, int iters, 
                  cudaEvent_t e1) {
   if (p.algo == ADFFT_ALGO_BLUESTEIN && !p.fold_ok && !p.tp_ok) return ADFFT_OK;   // nothing to choose
   const bool had_tp = p.tp_ok;
-  const Entry start{p.algo == ADFFT_ALGO_FOUR_STEP ? ADFFT_ALGO_FOUR_STEP : ADFFT_ALGO_FOLD, p.fold_choice, 0.0};
+  const Entry start{p.algo == ADFFT_ALGO_FOUR_STEP ? ADFFT_ALGO_FOUR_STEP : ADFFT_ALGO_FOLD, p.fold_choice, p.tp_A,
+                    0.0};
   const int saved_algo = p.algo;
   Entry best{};
   best.ms = -1.0;
@@ -148,19 +152,33 @@ int tune_uniform(Plan& p, const void* in, void* out, cudaStream_t s, int iters, 
       p.algo = saved_algo;
       return (int)ms;
     }
-    if (best.ms < 0.0 || ms < best.ms) best = Entry{ADFFT_ALGO_FOLD, p.fold_choice, ms};
+    if (best.ms < 0.0 || ms < best.ms) best = Entry{ADFFT_ALGO_FOLD, p.fold_choice, 0, ms};
   }
-  const int rc_tp = setup_twopass(p);
-  if (rc_tp == ADFFT_OK && prepare_precision(p) == ADFFT_OK) {
-    p.algo = ADFFT_ALGO_FOUR_STEP;
-    const double ms = time_forward(p, in, out, s, iters, e0, e1);
-    if (ms < 0.0) {
-      p.algo = saved_algo;
-      return (int)ms;
+  // the four-step form with every split Nc = A B it takes (B up to 2048)
+  {
+    int mode;
+    int64_t Nc, Mc;
+    core_shape(p, &mode, &Nc, &Mc);
+    const bool pow2 = Nc >= 4 && (Nc & (Nc - 1)) == 0 && mode != kLoadRealPlain;
+    for (int64_t A = pow2 ? Nc / 2 : 0; A >= 16 && Nc / A <= 2048; A >>= 1) {
+      if (p.tp_ok) release_twopass(p);
+      p.tp_force_A = A;
+      const int rc_tp = setup_twopass(p);
+      if (rc_tp == ADFFT_OK && prepare_precision(p) == ADFFT_OK) {
+        p.algo = ADFFT_ALGO_FOUR_STEP;
+        const double ms = time_forward(p, in, out, s, iters, e0, e1);
+        if (ms < 0.0) {
+          p.algo = saved_algo;
+          return (int)ms;
+        }
+        if (best.ms < 0.0 || ms < best.ms) best = Entry{ADFFT_ALGO_FOUR_STEP, FoldChoice{}, A, ms};
+      } else if (rc_tp != ADFFT_OK && rc_tp != ADFFT_ERR_UNSUPPORTED_SIZE) {
+        release_twopass(p);   // a partial set-up (allocation failure): drop it, tuning goes on
+      } else if (rc_tp != ADFFT_OK) {
+        release_twopass(p);
+      }
     }
-    if (best.ms < 0.0 || ms < best.ms) best = Entry{ADFFT_ALGO_FOUR_STEP, FoldChoice{}, ms};
-  } else if (rc_tp != ADFFT_OK && rc_tp != ADFFT_ERR_UNSUPPORTED_SIZE) {
-    release_twopass(p);   // a partial set-up (allocation failure): drop it, tuning goes on without it
+    p.tp_force_A = 0;
   }
   if (best.ms < 0.0) {
     p.algo = saved_algo;
@@ -276,13 +294,14 @@ bool parse_entry(Parser& ps, Key& k, Entry& en) {
     else if (name == "cluster") en.fold.cluster = (int)v, have |= 128;
     else if (name == "staged") en.fold.stage = (int)v, have |= 256;
     else if (name == "grid") en.fold.grid = (int)v;
+    else if (name == "four_step_a") en.tp_a = (int64_t)v;
     else if (name == "ms") en.ms = v;
   } while (ps.eat(','));
   if (!ps.eat('}')) return false;
   if (!have_dev || have != 511) return false;
   if (en.algo != ADFFT_ALGO_FOLD && en.algo != ADFFT_ALGO_FOUR_STEP) return false;
   if (en.fold.stage != 0 && en.fold.stage != 1) return false;
-  if (en.fold.grid < -1) return false;
+  if (en.fold.grid < -1 || en.tp_a < 0) return false;
   return true;
 }
 
@@ -368,9 +387,10 @@ int adfft_autotune_save(const char* path) {
       snprintf(buf, sizeof buf,
                ", \"N\": %lld, \"M\": %lld, \"batch\": %lld, \"dtype\": %d, \"precision\": %d, "
                "\"algo\": %d, \"fft_len\": %lld, \"cluster\": %d, \"staged\": %d, \"grid\": %d, "
-               "\"ms\": %.6g}",
+               "\"four_step_a\": %lld, \"ms\": %.6g}",
                (long long)k.N, (long long)k.M, (long long)k.batch, k.dtype, k.precision, e.algo,
-               (long long)e.fold.np, e.fold.cluster, e.fold.stage == 1 ? 1 : 0, e.fold.grid, e.ms);
+               (long long)e.fold.np, e.fold.cluster, e.fold.stage == 1 ? 1 : 0, e.fold.grid, (long long)e.tp_a,
+               e.ms);
       o += buf;
     }
   }

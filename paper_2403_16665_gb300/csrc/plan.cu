@@ -269,7 +269,10 @@ int setup_fold(Plan& p, const FoldChoice* forced) {
   return ADFFT_OK;
 }
 
-// Configure the two-pass (four-step) path for power-of-two Nc beyond one cluster.
+// Configure the two-pass (four-step) path for power-of-two Nc: Nc = A B, pass 1 the
+// alpha-DFTs of the B columns of length A, pass 2 the B-point FFTs.  Without a forced A
+// (p.tp_force_A == 0) the longest A whose pass-1 transform fits one CTA (each CTA then
+// reads its strided column once), else clusters of at most 4, then 8 CTAs.
 int setup_twopass(Plan& p) {
   int mode;
   int64_t Nc, Mc;
@@ -278,10 +281,14 @@ int setup_twopass(Plan& p) {
   if (mode == kLoadRealPlain || !is_pow2(Nc) || Nc < 4) return ADFFT_ERR_UNSUPPORTED_SIZE;
   const size_t esz = p.dbl ? 16 : 8;
   const int vpt = fused_values_per_thread(p.dbl);
-  for (int max_c : {4, 8}) {
+  const bool forced = p.tp_force_A > 0;
+  for (int max_c : {1, 4, 8, 16}) {
+    if (!forced && max_c == 16) break;
+    if (forced && max_c == 1) continue;
     for (int64_t A = Nc / 2; A >= 16; A >>= 1) {
       const int64_t B = Nc / A;
       if (B > 2048) break;
+      if (forced && A != p.tp_force_A) continue;
       if ((Mc * A) % Nc != 0) continue;
       const int64_t R1 = Mc * A / Nc;
       if (mode == kLoadRealPacked && (R1 % 2) != 0) continue;
@@ -883,6 +890,7 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
     info->cluster = 1;
   } else if (p.algo == ADFFT_ALGO_FOUR_STEP) {
     info->fft_len = p.tp_A * p.tp_B;      // the sub-FFT length, split A x B over two passes
+    info->four_step_a = (int32_t)p.tp_A;
     info->residues = p.tp1.args.P;
     info->fold = p.tp1.args.q;
     info->cluster = p.tp1.args.C;

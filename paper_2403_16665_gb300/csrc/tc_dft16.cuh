@@ -142,7 +142,12 @@ __device__ void stockham_pass_tc(const FusedArgs& a, V* buf, const TwTable<V>& t
       const float2 w[4] = {wa, cmul(wa, w1), wb, cmul(wb, w1)};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float2 v = ok ? src[idx4[e] * in_step] : make_float2(0.f, 0.f);
+        // pad16(j + i S) = pad16(j) + i (S + S/16) needs S a multiple of 16; shorter
+        // transforms index every element through pad16
+        float2 v = make_float2(0.f, 0.f);
+        if (ok)
+          v = (items_res >= 16) ? src[idx4[e] * in_step]
+                                : reinterpret_cast<const float2*>(buf)[rl * a.region + pad16(j + idx4[e] * items_res)];
         x[h][e] = cmul(v, w[e]);
       }
     }

@@ -25,7 +25,8 @@ def write(path, obj):
 
 def test_round_trip_and_merge(lib, tmp_path):
     adfft.autotune_clear()
-    e2 = dict(ENTRY, N=8192, M=20480, dtype=1, algo=3, fft_len=0, cluster=0, staged=0, grid=-1, ms=0.5)
+    e2 = dict(ENTRY, N=8192, M=20480, dtype=1, algo=3, fft_len=0, cluster=0, staged=0, grid=-1, four_step_a=1024,
+              ms=0.5)
     e3 = dict(ENTRY, device='other "gpu"\\x', batch=7)
     adfft.autotune_load(write(tmp_path / "a.json", {"adfft_autotune": 1, "entries": [ENTRY, e2]}))
     adfft.autotune_load(write(tmp_path / "b.json", {"adfft_autotune": 1, "entries": [e3]}))
@@ -40,6 +41,7 @@ def test_round_trip_and_merge(lib, tmp_path):
         e = entries[key(want)]
         for k in ("algo", "fft_len", "cluster", "staged", "grid"):
             assert e[k] == want[k], (k, e, want)
+        assert e["four_step_a"] == want.get("four_step_a", 0)
         assert abs(e["ms"] - want["ms"]) <= 1e-5 * want["ms"]
     # the saved file loads again; a later entry for the same key replaces the earlier one
     adfft.autotune_clear()
@@ -66,6 +68,7 @@ def test_round_trip_and_merge(lib, tmp_path):
     '{"adfft_autotune": 1, "entries": [' + json.dumps(ENTRY)[:-3] + ']}',                 # truncated
     '{"adfft_autotune": 1, "entries": [' + json.dumps(dict(ENTRY, staged=5)) + ']}',
     '{"adfft_autotune": 1, "entries": [' + json.dumps(dict(ENTRY, grid=-2)) + ']}',
+    '{"adfft_autotune": 1, "entries": [' + json.dumps(dict(ENTRY, four_step_a=-4)) + ']}',
 ])
 def test_rejects_malformed_files_and_merges_nothing(lib, tmp_path, text):
     adfft.autotune_clear()

@@ -333,3 +333,33 @@ def test_specialised_sub_fft_8192_shapes(N, alpha, B, cluster, staged):
     assert rel(X[sig][:, bins], ref) <= tol_for(M, False)
     m = np.arange(1, M)
     assert np.max(np.abs(X[0][M - m] - np.conj(X[0][m]))) <= 1e-5 * np.max(np.abs(X[0]))
+
+
+def test_autotune_four_step_split():
+    """A plan only the four-step form serves (N = 2^18 real, alpha = 16): the autotuner
+    times every split Nc = A B; the tuned plan agrees with the default one and with the
+    oracle on sampled bins, and the split is recorded in the cache."""
+    torch = _torch()
+    adfft.autotune_clear()
+    B, N, alpha = 2, 1 << 18, 16
+    M = N * alpha
+    x = make_input(adfft.R32, B, N, 99)
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(x).to(dev)
+    plan = adfft.Plan(N, batch=B, dtype=adfft.R32, M=M)
+    assert plan.info.passes == 2
+    X0 = forward(torch, plan, xt, M, False).cpu().numpy()
+    X = torch.empty((B, M), dtype=torch.complex64, device=dev)
+    plan.autotune(xt.data_ptr(), X.data_ptr(), iters=1)
+    info = plan.info
+    assert info.tuned == 1 and info.passes == 2 and info.four_step_a * (info.fft_len // info.four_step_a) == N // 2
+    X1 = forward(torch, plan, xt, M, False).cpu().numpy()
+    assert rel(X1, X0) <= 2 * tol_for(M, False)
+    bins = sample_bins(M, 500, 7)
+    ref = oracle.alpha_dft(x.astype(np.float64), M, bins=bins)
+    assert rel(X1[:, bins], ref) <= tol_for(M, False)
+    p2 = adfft.Plan(N, batch=B, dtype=adfft.R32, M=M)
+    assert p2.info.tuned == 1 and p2.info.four_step_a == info.four_step_a
+    X2 = forward(torch, p2, xt, M, False).cpu().numpy()
+    assert rel(X2, X1) <= 1e-7
+    adfft.autotune_clear()
