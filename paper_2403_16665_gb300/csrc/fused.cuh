@@ -249,13 +249,14 @@ __device__ __forceinline__ void first_pass(const FusedArgs& a, const void* u, co
       for (int i = 0; i < R; ++i) dst[SH::pad(j * R + i)] = acc[i];
     }
   };
-  if (items < (int)T) {
-    // fewer items per residue than threads: the threads take (residue, item) pairs of all
-    // the CTA's residues at once, so that none idles while the residues are done in turn
-    const int log_items = SH::logNp(a) - (R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5);
+  if (items < (int)T && (T % (unsigned)items) == 0) {
+    // fewer items per residue than threads: thread t keeps item j = t mod items and takes
+    // residues t / items, t / items + T / items, ... so that no thread idles while the
+    // residues are done in turn (the residue constants are computed once per residue)
+    const int rstep = (int)T / items;
+    const int j = threadIdx.x % items;
 #pragma unroll 1
-    for (int t = threadIdx.x; t < rpc * items; t += T) {
-      const int rl = t >> log_items, j = t & (items - 1);
+    for (int rl = threadIdx.x / items; rl < rpc; rl += rstep) {
       const unsigned long long sr = (unsigned long long)s * (unsigned)(r0 + rl);
       const V c1 = tab((unsigned)((sr * (unsigned)items) % Mt));
       const V g1 = tab((unsigned)((sr * (unsigned)Np) % Mt));
