@@ -212,7 +212,8 @@ int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *s
  * can be resident at once, each looping over signals; the two-pass form only
  * where no single-pass shape fits.
  *
- * adfft_plan_autotune times the forward transform of the plan for every
+ * adfft_plan_autotune times the forward transform of the plan (flags 0) or the
+ * forward transform and its adjoint (ADFFT_TUNE_WITH_ADJOINT) for every
  * candidate launch shape (sub-FFT length, cluster size, input staging, a
  * resident-size or one-per-signal grid; the two-pass form, with every split
  * of its transform length into A*B, where it applies) with `iters` timed launches each (1..100;
@@ -231,7 +232,14 @@ int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *s
  * adfft_autotune_clear empties the cache.  The cache is guarded by a mutex;
  * a plan itself is not thread-safe.
  */
-int adfft_plan_autotune(adfft_plan_t plan, const void *d_in, void *d_out, void *stream, int iters);
+int adfft_plan_autotune(adfft_plan_t plan, const void *d_in, void *d_out, void *stream, int iters,
+                        int flags);
+
+/* Flags of adfft_plan_autotune: time each candidate on a forward transform followed by
+ * its adjoint (the backward pass of a training step) instead of the forward alone.  The
+ * adjoint writes into a temporary device buffer of the input's size that the call
+ * allocates and frees.  The cache keeps one entry per key: the last tuning wins. */
+#define ADFFT_TUNE_WITH_ADJOINT 1
 
 /*
  * Set the fold form's launch shape by hand (the autotuner's candidates):

@@ -19,6 +19,8 @@ R32, C64, R64, C128 = 0, 1, 2, 3
 ALGO_AUTO, ALGO_FOLD, ALGO_BLUESTEIN, ALGO_FOUR_STEP = 0, 1, 2, 3
 # adfft_precision_t
 PREC_NATIVE, PREC_FP16X2, PREC_BF16X3 = 0, 1, 2
+# adfft_plan_autotune flags
+TUNE_WITH_ADJOINT = 1
 
 STATUS = {
     0: "ADFFT_OK", -1: "ADFFT_ERR_INVALID_ARG", -2: "ADFFT_ERR_INVALID_ALPHA",
@@ -84,7 +86,7 @@ def load(path: str | None = None):
         "adfft_execute_host": ([vp, vp, vp, vp], i32),
         "adfft_plan_sync_status": ([vp, vp], i32),
         "adfft_execute_noalloc": ([i64, i64, i64, i32, vp, vp, vp], i32),
-        "adfft_plan_autotune": ([vp, vp, vp, vp, i32], i32),
+        "adfft_plan_autotune": ([vp, vp, vp, vp, i32, i32], i32),
         "adfft_autotune_save": ([ctypes.c_char_p], i32),
         "adfft_autotune_load": ([ctypes.c_char_p], i32),
         "adfft_autotune_clear": ([], i32),
@@ -170,10 +172,12 @@ class Plan:
                                            ctypes.c_void_p(_stream_handle(stream))),
                "adfft_execute_host")
 
-    def autotune(self, d_in: int, d_out: int, stream=None, iters=0):
-        """Time the candidate launch shapes on these buffers and keep the fastest (d_out is overwritten)."""
+    def autotune(self, d_in: int, d_out: int, stream=None, iters=0, with_adjoint=False):
+        """Time the candidate launch shapes on these buffers and keep the fastest (d_out is
+        overwritten); with_adjoint: time forward + adjoint steps (training)."""
         _check(self.lib.adfft_plan_autotune(self._h, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
-                                            ctypes.c_void_p(_stream_handle(stream)), int(iters)),
+                                            ctypes.c_void_p(_stream_handle(stream)), int(iters),
+                                            TUNE_WITH_ADJOINT if with_adjoint else 0),
                "adfft_plan_autotune")
         self.info = self.get_info()
 

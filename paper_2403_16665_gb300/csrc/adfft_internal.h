@@ -155,7 +155,7 @@ constexpr int kTuneMaxFold = 16;      // largest fold factor q the autotuner and
 
 // Autotuner (autotune.cu): apply a cached choice at plan creation; time and choose.
 void autotune_apply_cached(Plan& p);
-int autotune_plan(Plan& p, const void* in, void* out, cudaStream_t s, int iters);
+int autotune_plan(Plan& p, const void* in, void* out, cudaStream_t s, int iters, int flags);
 void ragged_invalidate(Plan& p);   // drop captured graphs (launch shapes changed)
 
 // Launch the plan's forward / adjoint kernels (no argument checks).

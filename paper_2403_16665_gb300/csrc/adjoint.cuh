@@ -37,6 +37,12 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
   for (int i = threadIdx.x; i < tw_n; i += blockDim.x) tw_s[i] = reinterpret_cast<const V*>(a.tw)[i];
   __syncthreads();
   TwTable<V> tab{tw_s, tw_s + a.tw_lo_n, a.tw_bits, (1u << a.tw_bits) - 1u};
+  // the first signal's prologue stores into the other CTAs' shared memory: every CTA of
+  // the cluster must be running before any CTA accesses another's shared memory
+  if (a.C > 1) {
+    cluster_arrive();
+    cluster_wait();
+  }
 
   const int c = (int)blockIdx.x;
   const int r0 = c * SH::rpc(a);

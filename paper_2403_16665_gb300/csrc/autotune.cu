@@ -114,13 +114,19 @@ std::vector<FoldChoice> fold_candidates(const Plan& p) {
   return out;
 }
 
-// Mean time per forward launch of the plan as configured now (ms), or a negative status.
-double time_forward(Plan& p, const void* in, void* out, cudaStream_t s, int iters, cudaEvent_t e0,
+// Mean time per forward launch of the plan as configured now (ms), or a negative status;
+// with xb != nullptr each step is a forward and the adjoint of its spectrum into xb.
+double time_forward(Plan& p, const void* in, void* out, void* xb, cudaStream_t s, int iters, cudaEvent_t e0,
                     cudaEvent_t e1) {
-  int rc = launch_forward(p, in, out, s);   // warm-up (also first-touch of tables)
+  auto step = [&]() {
+    int r = launch_forward(p, in, out, s);
+    if (r == ADFFT_OK && xb) r = launch_adjoint(p, out, xb, s);
+    return r;
+  };
+  int rc = step();   // warm-up (also first-touch of tables)
   if (rc != ADFFT_OK) return (double)rc;
   if (cudaEventRecord(e0, s) != cudaSuccess) return (double)ADFFT_ERR_CUDA;
-  for (int i = 0; i < iters && rc == ADFFT_OK; ++i) rc = launch_forward(p, in, out, s);
+  for (int i = 0; i < iters && rc == ADFFT_OK; ++i) rc = step();
   if (rc != ADFFT_OK) return (double)rc;
   if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
     cudaGetLastError();
@@ -134,7 +140,7 @@ double time_forward(Plan& p, const void* in, void* out, cudaStream_t s, int iter
   return (double)ms / iters;
 }
 
-int tune_uniform(Plan& p, const void* in, void* out, cudaStream_t s, int iters, cudaEvent_t e0,
+int tune_uniform(Plan& p, const void* in, void* out, void* xb, cudaStream_t s, int iters, cudaEvent_t e0,
                  cudaEvent_t e1) {
   if (p.algo == ADFFT_ALGO_BLUESTEIN && !p.fold_ok && !p.tp_ok) return ADFFT_OK;   // nothing to choose
   const bool had_tp = p.tp_ok;
@@ -147,7 +153,7 @@ int tune_uniform(Plan& p, const void* in, void* out, cudaStream_t s, int iters, 
     if (setup_fold(p, &c) != ADFFT_OK) continue;   // does not fit (or cannot launch): skip
     if (prepare_precision(p) != ADFFT_OK) continue;
     p.algo = ADFFT_ALGO_FOLD;
-    const double ms = time_forward(p, in, out, s, iters, e0, e1);
+    const double ms = time_forward(p, in, out, xb, s, iters, e0, e1);
     if (ms < 0.0) {
       p.algo = saved_algo;
       return (int)ms;
@@ -166,7 +172,7 @@ int tune_uniform(Plan& p, const void* in, void* out, cudaStream_t s, int iters, 
       const int rc_tp = setup_twopass(p);
       if (rc_tp == ADFFT_OK && prepare_precision(p) == ADFFT_OK) {
         p.algo = ADFFT_ALGO_FOUR_STEP;
-        const double ms = time_forward(p, in, out, s, iters, e0, e1);
+        const double ms = time_forward(p, in, out, xb, s, iters, e0, e1);
         if (ms < 0.0) {
           p.algo = saved_algo;
           return (int)ms;
@@ -324,22 +330,37 @@ void autotune_apply_cached(Plan& p) {
   if (apply(p, e) == ADFFT_OK) p.tuned = true;   // else the default shape stays
 }
 
-int autotune_plan(Plan& p, const void* in, void* out, cudaStream_t s, int iters) {
+int autotune_plan(Plan& p, const void* in, void* out, cudaStream_t s, int iters, int flags) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
     if (e0) cudaEventDestroy(e0);
     return ADFFT_ERR_CUDA;
   }
+  // forward + adjoint: the adjoint writes into a temporary buffer of the input's size
+  void* xb = nullptr;
+  if (flags & ADFFT_TUNE_WITH_ADJOINT) {
+    const cudaError_t e = cudaMalloc(&xb, std::max<size_t>(16, p.in_bytes()));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return e == cudaErrorMemoryAllocation ? ADFFT_ERR_OOM : ADFFT_ERR_CUDA;
+    }
+  }
   int rc = ADFFT_OK;
   if (p.ragged) {
     for (auto* sp : p.r_sub) {
-      rc = tune_uniform(sp->p, in, out, s, iters, e0, e1);
+      rc = tune_uniform(sp->p, in, out, xb, s, iters, e0, e1);
       if (rc != ADFFT_OK) break;
     }
     ragged_invalidate(p);   // the next execute captures the new shapes
   } else {
-    rc = tune_uniform(p, in, out, s, iters, e0, e1);
+    rc = tune_uniform(p, in, out, xb, s, iters, e0, e1);
+  }
+  if (xb) {
+    cudaStreamSynchronize(s);
+    cudaFree(xb);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -352,8 +373,9 @@ using adfft::Plan;
 
 extern "C" {
 
-int adfft_plan_autotune(adfft_plan_t plan, const void* d_in, void* d_out, void* stream, int iters) {
-  if (!plan || !d_in || !d_out || iters < 0 || iters > 100) return ADFFT_ERR_INVALID_ARG;
+int adfft_plan_autotune(adfft_plan_t plan, const void* d_in, void* d_out, void* stream, int iters, int flags) {
+  if (!plan || !d_in || !d_out || iters < 0 || iters > 100 || (flags & ~ADFFT_TUNE_WITH_ADJOINT))
+    return ADFFT_ERR_INVALID_ARG;
   Plan& p = plan->p;
   if (((uintptr_t)d_in & 15u) || ((uintptr_t)d_out & 15u)) return ADFFT_ERR_MISALIGNED;
   const size_t ni = p.in_bytes(), no = p.out_bytes();
@@ -366,7 +388,7 @@ int adfft_plan_autotune(adfft_plan_t plan, const void* d_in, void* d_out, void* 
     return ADFFT_ERR_CUDA;
   }
   if (cs != cudaStreamCaptureStatusNone) return ADFFT_ERR_NOT_SUPPORTED;
-  return adfft::autotune_plan(p, d_in, d_out, s, iters ? iters : 3);
+  return adfft::autotune_plan(p, d_in, d_out, s, iters ? iters : 3, flags);
 }
 
 int adfft_autotune_save(const char* path) {

@@ -134,9 +134,9 @@ def ragged(args):
     Xr = X.clone()
     if args.tune:
         Xt = torch.empty_like(X)
-        plan.autotune(x.data_ptr(), Xt.data_ptr())
-        report("ragged plan, tuned, forward", _time(lambda: plan.execute(x.data_ptr(), Xt.data_ptr()), args.iters))
-        report("ragged plan, tuned, adjoint",
+        plan.autotune(x.data_ptr(), Xt.data_ptr(), with_adjoint=True)
+        report("ragged plan, tuned (fwd + adj), forward", _time(lambda: plan.execute(x.data_ptr(), Xt.data_ptr()), args.iters))
+        report("ragged plan, tuned (fwd + adj), adjoint",
                _time(lambda: plan.execute_adjoint(g.data_ptr(), xb.data_ptr()), args.iters))
         d = (torch.linalg.norm(Xt - Xr) / torch.linalg.norm(Xr)).item()
         print("ragged tuned vs untuned forward: rel difference %.2e" % d)

@@ -95,5 +95,5 @@ def test_missing_file_and_null_arguments(lib, tmp_path):
         adfft.autotune_load(str(tmp_path / "does_not_exist.json"))
     assert lib.adfft_autotune_load(None) == -1
     assert lib.adfft_autotune_save(None) == -1
-    assert lib.adfft_plan_autotune(None, None, None, None, 0) == -1
+    assert lib.adfft_plan_autotune(None, None, None, None, 0, 0) == -1
     assert lib.adfft_plan_set_launch_shape(None, 0, 0, -1, 0) == -1

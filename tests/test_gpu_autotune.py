@@ -273,7 +273,7 @@ def test_autotune_ragged():
     X0 = torch.empty(int(plan.out_off[-1]), dtype=torch.complex64, device=dev)
     plan.execute(x.data_ptr(), X0.data_ptr())
     X = torch.empty_like(X0)
-    plan.autotune(x.data_ptr(), X.data_ptr(), iters=1)
+    plan.autotune(x.data_ptr(), X.data_ptr(), iters=1, with_adjoint=True)   # forward + backward steps
     assert plan.info.tuned == 1
     X1 = torch.empty_like(X0)
     plan.execute(x.data_ptr(), X1.data_ptr())   # captures a new graph with the tuned shapes
