@@ -136,6 +136,21 @@ def test_execute_host_matches_device_path():
     assert np.array_equal(hX.numpy(), dev_out)
 
 
+@pytest.mark.parametrize("B,N,M", [(37, 1024, 8192), (20, 16384, 131072)])
+def test_execute_host_larger_batches_match_device_path(B, N, M):
+    """Host buffers: copy in, transform, copy out, on larger batches and the benchmark
+    shape: same bits as the device path, twice in a row."""
+    torch = _torch()
+    x = make_input(B, N, adfft.R32, 13)
+    dev_out, plan = run_plan(torch, x, M, adfft.R32)
+    hx = torch.from_numpy(x).pin_memory()
+    hX = torch.empty((B, M), dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        hX.zero_()
+        plan.execute_host(hx.data_ptr(), hX.data_ptr())
+        assert np.array_equal(hX.numpy(), dev_out)
+
+
 def test_tone_on_fine_grid_gpu():
     """A tone at j/(alpha T): X_j = T A and the bins j + k alpha vanish (closed form)."""
     torch = _torch()
