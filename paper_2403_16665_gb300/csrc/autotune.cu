@@ -147,6 +147,12 @@ int tune_uniform(Plan& p, const void* in, void* out, void* xb, cudaStream_t s, i
   const Entry start{p.algo == ADFFT_ALGO_FOUR_STEP ? ADFFT_ALGO_FOUR_STEP : ADFFT_ALGO_FOLD, p.fold_choice, p.tp_A,
                     0.0};
   const int saved_algo = p.algo;
+  // a failed timing run leaves the plan as it was before tuning (then reports the error)
+  auto restore = [&](int err) {
+    apply(p, start);
+    p.algo = saved_algo;
+    return err;
+  };
   Entry best{};
   best.ms = -1.0;
   for (const FoldChoice& c : fold_candidates(p)) {
@@ -154,10 +160,7 @@ int tune_uniform(Plan& p, const void* in, void* out, void* xb, cudaStream_t s, i
     if (prepare_precision(p) != ADFFT_OK) continue;
     p.algo = ADFFT_ALGO_FOLD;
     const double ms = time_forward(p, in, out, xb, s, iters, e0, e1);
-    if (ms < 0.0) {
-      p.algo = saved_algo;
-      return (int)ms;
-    }
+    if (ms < 0.0) return restore((int)ms);
     if (best.ms < 0.0 || ms < best.ms) best = Entry{ADFFT_ALGO_FOLD, p.fold_choice, 0, ms};
   }
   // the four-step form with every split Nc = A B it takes (B up to 2048)
@@ -174,8 +177,8 @@ int tune_uniform(Plan& p, const void* in, void* out, void* xb, cudaStream_t s, i
         p.algo = ADFFT_ALGO_FOUR_STEP;
         const double ms = time_forward(p, in, out, xb, s, iters, e0, e1);
         if (ms < 0.0) {
-          p.algo = saved_algo;
-          return (int)ms;
+          p.tp_force_A = 0;
+          return restore((int)ms);
         }
         if (best.ms < 0.0 || ms < best.ms) best = Entry{ADFFT_ALGO_FOUR_STEP, FoldChoice{}, A, ms};
       } else if (rc_tp != ADFFT_OK && rc_tp != ADFFT_ERR_UNSUPPORTED_SIZE) {
