@@ -47,16 +47,15 @@ cudaError_t twopass_prepare(const TwoPassLaunch& L) {
   return e;
 }
 
-// Adjoint of the second pass: spectrum g -> scratch rows.  One CTA per block of
-// W columns out of all R1 (no mirror pairing); the adjoint uses only the first W
-// column regions of the launch's shared-memory layout.
+// Adjoint of the second pass: spectrum g -> scratch rows.  The forward pass's
+// geometry: one CTA per block of W columns (packed real input: W column pairs
+// m1, R1 - m1, 2 W column regions of shared memory).
 cudaError_t twopass_adjoint_launch(const TwoPassLaunch& L, const void* g, void* scratch, cudaStream_t stream) {
   TwoPassArgs t = L.args;
   t.out = const_cast<void*>(g);
   t.scratch = scratch;
-  t.f.RPC = t.W;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((t.R1 + t.W - 1) / t.W), L.grid_y, 1);
+  cfg.gridDim = dim3(L.grid_x, L.grid_y, 1);
   cfg.blockDim = dim3(L.threads, 1, 1);
   cfg.dynamicSmemBytes = L.smem;
   cfg.stream = stream;

@@ -144,11 +144,17 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
 }
 
 // Adjoint of the second pass (first step of the two-pass adjoint): for a block
-// of W columns m1, forms the (Hermitian-folded, for packed real input)
+// of columns m1, forms the (Hermitian-folded, for packed real input)
 // spectrum ub_{m1 + R1 m2}, runs the inverse B-point DFT over m2 as
 // conj(FFT(conj(.))), multiplies by conj(W_Mc^{m1 b}) and the scale S, and
 // writes scratch row b.  The first pass's adjoint (adjoint kernel, kColumns
 // mode) then takes the rows to the input samples u_{B a + b}.
+// For packed real input the fold of bin j reads g_{M-j} and g_{Mc-j}, which lie
+// in the mirror column (R1 - m1) mod R1; a CTA therefore takes W column pairs
+// (m1 <= R1/2 in slots 0..W-1, the mirrors in slots W..2W-1, as the forward
+// pass does), so that each spectrum value is fetched from HBM once and its
+// second read hits in L2.  Columns 0 and R1/2 are their own mirrors and use
+// only the first slot.
 //   t.out     : the spectrum g [batch][M] (read), offsets from t.f.offs
 //   t.scratch : [batch][B][R1] (written)
 template <typename V, int VPT, int R0>
@@ -170,23 +176,34 @@ __global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoP
   const unsigned long long Mc = (unsigned long long)t.Mc;
   const unsigned long long M = (unsigned long long)t.M;
   const unsigned long long sM = M / Mc;   // W_Mc^e = W_M^{sM e}
+  const unsigned npairs = (unsigned)(t.real_packed ? R1 / 2 + 1 : R1);
   const unsigned p0 = blockIdx.x * W;
-  const unsigned np = (unsigned)min((unsigned long long)W, R1 - p0);
+  const unsigned np = min(W, npairs - p0);
+  const unsigned ncol = t.real_packed ? 2 * W : W;   // = a.RPC
   const unsigned T = blockDim.x;
   const Rl S = (Rl)t.scale;
+  // column of slot s, or -1 for an empty slot (past the last pair, or the mirror of a self-paired column)
+  auto slot_col = [&](unsigned s) -> long long {
+    const unsigned pw = (s < W) ? s : s - W;
+    if (pw >= np) return -1;
+    const unsigned long long m1 = p0 + pw;
+    if (s < W) return (long long)m1;
+    if (m1 == 0 || 2 * m1 == R1) return -1;
+    return (long long)(R1 - m1);
+  };
 
   for (long long sig = blockIdx.y; sig < t.batch; sig += gridDim.y) {
     const V* g = reinterpret_cast<const V*>(t.out) + (t.f.offs ? t.f.offs[2 * sig + 1] : sig * t.M);
     // (UA elements' loads in flight per thread before they are combined and stored)
     constexpr int UA = sizeof(V) == 16 ? 1 : 2;
-    for (unsigned i0 = threadIdx.x; i0 < W * B; i0 += T * UA) {
+    for (unsigned i0 = threadIdx.x; i0 < ncol * B; i0 += T * UA) {
       V g0[UA], g1[UA], g2[UA], g3[UA];
 #pragma unroll
       for (int e = 0; e < UA; ++e) {
         const unsigned idx = i0 + e * T;
-        const unsigned w = idx % W, m2 = idx / W;
-        if (idx < W * B && w < np) {
-          const unsigned long long j = p0 + w + R1 * m2;
+        const long long col = (idx < ncol * B) ? slot_col(idx % ncol) : -1;
+        if (col >= 0) {
+          const unsigned long long j = (unsigned long long)col + R1 * (idx / ncol);
           g0[e] = __ldg(g + j);
           if (t.real_packed) {
             g1[e] = __ldg(g + j + Mc);
@@ -198,11 +215,12 @@ __global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoP
 #pragma unroll
       for (int e = 0; e < UA; ++e) {
         const unsigned idx = i0 + e * T;
-        if (idx >= W * B) continue;
-        const unsigned w = idx % W, m2 = idx / W;
+        if (idx >= ncol * B) continue;
+        const unsigned w = idx % ncol, m2 = idx / ncol;
+        const long long col = slot_col(w);
         V v = czero<V>();
-        if (w < np) {
-          const unsigned long long j = p0 + w + R1 * m2;
+        if (col >= 0) {
+          const unsigned long long j = (unsigned long long)col + R1 * m2;
           if (t.real_packed) {
             const V h0 = cscale(cadd(g0[e], cconj(g2[e])), (Rl)0.5);
             const V h1 = cscale(cadd(g1[e], cconj(g3[e])), (Rl)0.5);
@@ -231,10 +249,11 @@ __global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoP
       }
     }
     V* rows = reinterpret_cast<V*>(const_cast<void*>(t.scratch)) + (size_t)sig * B * R1;
-    for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
-      const unsigned w = idx % W, b = idx / W;
-      if (w >= np) continue;
-      const unsigned long long m1 = p0 + w;
+    for (unsigned idx = threadIdx.x; idx < ncol * B; idx += T) {
+      const unsigned w = idx % ncol, b = idx / ncol;
+      const long long col = slot_col(w);
+      if (col < 0) continue;
+      const unsigned long long m1 = (unsigned long long)col;
       const V y = cconj(buf[w * a.region + pad16((int)b)]);
       const unsigned long long e = ((m1 * b) % Mc) * sM;
       rows[(size_t)b * R1 + m1] = cscale(cmulc(y, tw_global<V>(t.wM, t.wM_lo_n, t.wM_bits, e)), S);
