@@ -61,7 +61,8 @@ def main():
     if args.shape:
         plan.set_launch_shape(*(int(v) for v in args.shape.split(",")))
     if args.tune:
-        plan.autotune(x.data_ptr(), X.data_ptr())
+        # with --adjoint the tuner times forward + adjoint steps (the adjoint's output overwrites x)
+        plan.autotune(x.data_ptr(), X.data_ptr(), with_adjoint=args.adjoint)
     g = torch.empty_like(x) if args.adjoint else None
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -77,11 +78,11 @@ def main():
     ms = e0.elapsed_time(e1) / max(1, args.iters)
     info = plan.info
     nbytes = x.numel() * x.element_size() + B * M * X.element_size()
-    print("workload=%s B=%d N=%d M=%d algo=%d fft_len=%d P=%d q=%d C=%d staged=%d grid=%d tuned=%d passes=%d "
+    print("workload=%s B=%d N=%d M=%d algo=%d fft_len=%d A=%d P=%d q=%d C=%d staged=%d grid=%d tuned=%d passes=%d "
           "prec=%d adjoint=%d  "
           "%.4f ms/transform  %.1f GB/s (input + output bytes)  %.3e points/s"
-          % (args.workload, B, N, M, info.algo, info.fft_len, info.residues, info.fold, info.cluster, info.staged,
-             info.grid, info.tuned, info.passes,
+          % (args.workload, B, N, M, info.algo, info.fft_len, info.four_step_a, info.residues, info.fold,
+             info.cluster, info.staged, info.grid, info.tuned, info.passes,
              args.prec, int(args.adjoint), ms, nbytes / ms / 1e6, B * M / ms * 1e3))
 
 
