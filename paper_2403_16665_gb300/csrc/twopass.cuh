@@ -26,7 +26,7 @@ struct TwoPassArgs {
   int B, logB;
   long long R1;         // row length alpha A
   long long Mc, M;
-  int W;                // column pairs per CTA
+  int W;                // column pairs per CTA (4, 8 or 16: a power of two, as is B)
   int real_packed;
   const void* wM;       // two-level W_M table (global memory), for the real unpacking
   int wM_bits, wM_lo_n;
@@ -62,11 +62,12 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
   const unsigned np = min(W, npairs - p0);
   const unsigned T = blockDim.x;
   const Rl S = (Rl)t.scale;
+  // columns 0..W-1: m1 = p0 + w;  W..2W-1: the mirrors (R1 - m1) mod R1
+  const unsigned ncol = t.real_packed ? 2 * W : W;
+  const unsigned lw = 31 - __clz(W), lncol = 31 - __clz(ncol);   // W, ncol: powers of two
 
   for (long long sig = blockIdx.y; sig < t.batch; sig += gridDim.y) {
     const V* src = reinterpret_cast<const V*>(t.scratch) + (size_t)sig * B * R1;
-    // columns 0..W-1: m1 = p0 + w;  W..2W-1: the mirrors (R1 - m1) mod R1
-    const unsigned ncol = t.real_packed ? 2 * W : W;
     // (8 loads in flight per thread before the shared-memory stores)
     constexpr int UL = 8;
     for (unsigned i0 = threadIdx.x; i0 < ncol * B; i0 += T * UL) {
@@ -74,19 +75,19 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
 #pragma unroll
       for (int e = 0; e < UL; ++e) {
         const unsigned idx = i0 + e * T;
-        const unsigned w = idx % ncol, b = idx / ncol;   // consecutive threads: consecutive columns
+        const unsigned w = idx & (ncol - 1), b = idx >> lncol;   // consecutive threads: consecutive columns
         v[e] = czero<V>();
         const unsigned pw = (w < W) ? w : w - W;
         if (idx < ncol * B && pw < np) {
           const unsigned long long m1 = p0 + pw;
-          const unsigned long long col = (w < W) ? m1 : (R1 - m1) % R1;
+          const unsigned long long col = (w < W) ? m1 : (m1 ? R1 - m1 : 0);
           v[e] = __ldg(src + (size_t)b * R1 + col);
         }
       }
 #pragma unroll
       for (int e = 0; e < UL; ++e) {
         const unsigned idx = i0 + e * T;
-        if (idx < ncol * B) buf[(idx % ncol) * a.region + pad16((int)(idx / ncol))] = v[e];
+        if (idx < ncol * B) buf[(idx & (ncol - 1)) * a.region + pad16((int)(idx >> lncol))] = v[e];
       }
     }
     __syncthreads();
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
     if (t.real_packed) {
       // item (pair w, m2): j = m1 + R1 m2 and its partner in the mirror column
       for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
-        const unsigned w = idx % W, m2 = idx / W;
+        const unsigned w = idx & (W - 1), m2 = idx >> lw;
         if (w >= np) continue;
         const unsigned long long m1 = p0 + w;
         // columns 0 and R1/2 pair with themselves: only half of their m2 are leaders
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(512) twopass_columns_kernel(const TwoPassArgs 
       }
     } else {
       for (unsigned idx = threadIdx.x; idx < W * B; idx += T) {
-        const unsigned w = idx % W, m2 = idx / W;
+        const unsigned w = idx & (W - 1), m2 = idx >> lw;
         if (w >= np) continue;
         const unsigned long long j = p0 + w + R1 * m2;
         out[j] = cscale(buf[w * a.region + pad16((int)m2)], S);
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoP
   const unsigned p0 = blockIdx.x * W;
   const unsigned np = min(W, npairs - p0);
   const unsigned ncol = t.real_packed ? 2 * W : W;   // = a.RPC
+  const unsigned lncol = 31 - __clz(ncol);           // W, ncol: powers of two
   const unsigned T = blockDim.x;
   const Rl S = (Rl)t.scale;
   // column of slot s, or -1 for an empty slot (past the last pair, or the mirror of a self-paired column)
@@ -201,13 +203,13 @@ __global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoP
 #pragma unroll
       for (int e = 0; e < UA; ++e) {
         const unsigned idx = i0 + e * T;
-        const long long col = (idx < ncol * B) ? slot_col(idx % ncol) : -1;
+        const long long col = (idx < ncol * B) ? slot_col(idx & (ncol - 1)) : -1;
         if (col >= 0) {
-          const unsigned long long j = (unsigned long long)col + R1 * (idx / ncol);
+          const unsigned long long j = (unsigned long long)col + R1 * (idx >> lncol);
           g0[e] = __ldg(g + j);
           if (t.real_packed) {
             g1[e] = __ldg(g + j + Mc);
-            g2[e] = __ldg(g + (M - j) % M);
+            g2[e] = __ldg(g + (j ? M - j : 0));
             g3[e] = __ldg(g + (Mc - j));
           }
         }
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoP
       for (int e = 0; e < UA; ++e) {
         const unsigned idx = i0 + e * T;
         if (idx >= ncol * B) continue;
-        const unsigned w = idx % ncol, m2 = idx / ncol;
+        const unsigned w = idx & (ncol - 1), m2 = idx >> lncol;
         const long long col = slot_col(w);
         V v = czero<V>();
         if (col >= 0) {
@@ -250,12 +252,12 @@ __global__ void __launch_bounds__(512) twopass_adjoint_columns_kernel(const TwoP
     }
     V* rows = reinterpret_cast<V*>(const_cast<void*>(t.scratch)) + (size_t)sig * B * R1;
     for (unsigned idx = threadIdx.x; idx < ncol * B; idx += T) {
-      const unsigned w = idx % ncol, b = idx / ncol;
+      const unsigned w = idx & (ncol - 1), b = idx >> lncol;
       const long long col = slot_col(w);
       if (col < 0) continue;
       const unsigned long long m1 = (unsigned long long)col;
       const V y = cconj(buf[w * a.region + pad16((int)b)]);
-      const unsigned long long e = ((m1 * b) % Mc) * sM;
+      const unsigned long long e = m1 * b * sM;   // m1 b < R1 B = Mc
       rows[(size_t)b * R1 + m1] = cscale(cmulc(y, tw_global<V>(t.wM, t.wM_lo_n, t.wM_bits, e)), S);
     }
     __syncthreads();
