@@ -324,6 +324,22 @@ def run_native(args):
     return 0
 
 
+def free_port():
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def spawn_ranks(n):
+    """--gpus n > 1 without a torchrun environment: relaunch this command as n ranks (one
+    per GPU, 127.0.0.1 rendezvous) and return the launcher's exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(n),
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()),
+           os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,6 +351,15 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.gpus < 1:
+        ap.error("--gpus must be >= 1")
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        return spawn_ranks(args.gpus)
+    world = dist_env()[0]
+    if world != args.gpus and "WORLD_SIZE" in os.environ and "--gpus" in sys.argv:
+        # the launcher's world size is what runs (and what n_gpus reports)
+        print("bench.py: --gpus %d under WORLD_SIZE=%d; using %d ranks" % (args.gpus, world, world),
+              file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

@@ -126,10 +126,12 @@ adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dty
  * Ragged plan: `count` signals with their own N[i] and alpha[i] (each as in
  * adfft_plan_create), packed back to back: signal i occupies input elements
  * [in_off[i], in_off[i] + N[i]) and output bins [out_off[i], out_off[i] + M[i]),
- * offsets as returned by adfft_plan_offsets.  The forward transform of the
- * whole set is one persistent kernel launch over a queue of (signal, residue
- * group) tiles, replayed from a CUDA graph captured at the first execute on
- * a given stream.  Only ADFFT_R32 and ADFFT_C64 are accepted.
+ * offsets as returned by adfft_plan_offsets.  Signals are grouped into shape
+ * classes of equal (N, M); each class is one persistent launch of the fused
+ * kernel (its clusters loop over the class's signals through a device table of
+ * offsets), and all class launches, forked over internal streams, are captured
+ * into one CUDA graph at the first execute for a given buffer pair and
+ * replayed by later executes.  Only ADFFT_R32 and ADFFT_C64 are accepted.
  */
 adfft_plan_t adfft_plan_create_ragged(const int64_t *N, const double *alpha, int64_t count,
                                       int dtype);
@@ -287,7 +289,9 @@ int adfft_autotune_clear(void);
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) once for that device; make that first call before
  * any stream capture begins.  Every call reuses the same array and leaves the
- * last call's contents in it; nothing in it needs to start at zero.  Calls
+ * last call's contents in it; nothing in it needs to start at zero.  The
+ * tables are rewritten (four small kernels) only when a call's sizes differ
+ * from those of the previous call on the same device.  Calls
  * whose work overlaps on the GPU (for example on two streams) race on the
  * array and produce wrong results: serialise them.
  */

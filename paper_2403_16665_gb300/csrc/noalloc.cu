@@ -29,6 +29,9 @@ static __device__ __align__(256) unsigned char g_noalloc_mem[kNoAllocTableBytes 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_noalloc_addr[kMaxDevices];   // device address of g_noalloc_mem, per device, once set up
+// Sizes (R1, Mc, B, M) whose tables the array holds on each device, so that consecutive
+// calls with the same sizes do not rewrite them; all zero = none.  Guarded by g_setup_mutex.
+long long g_table_key[kMaxDevices][4];
 
 int64_t gcd_i64(int64_t a, int64_t b) {
   while (b) {
@@ -82,12 +85,13 @@ cudaError_t launch_table(unsigned char* base, const Table& t, long long X, cudaS
 }
 
 // One-time set-up for the current device: device address of the static array.
-int device_setup(void** addr) {
+int device_setup(void** addr, int* dev_out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return ADFFT_ERR_CUDA;
   }
+  *dev_out = dev;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
@@ -197,7 +201,14 @@ extern "C" int adfft_execute_noalloc(int64_t N, int64_t M, int64_t batch, int dt
       L1.mode = kColumns;
       L1.r0 = 1 << lr0;
       L1.dbl = false;
-      L1.threads = std::max(32, (int)(((P / C) * Np / kVpt + 31) / 32 * 32));
+      // the epilogue gives every residue at least one thread of each CTA (threads >= P),
+      // as the plan path does; a shape that would need more than kThreads is skipped
+      {
+        const int64_t t1 = std::max<int64_t>(((P / C) * Np + kVpt - 1) / kVpt, P);
+        const int64_t t1r = std::max<int64_t>(32, (t1 + 31) / 32 * 32);
+        if (t1r > kThreads) continue;
+        L1.threads = (int)t1r;
+      }
       L1.grid_y = (int)std::min<int64_t>(batch * B, 65535);
       L1.smem = (size_t)fused_smem_layout(tw1_n, 0, a.RPC, a.region, 8).total;
       if (C > 1 && fused_max_active_clusters(L1) < 1) continue;
@@ -249,7 +260,8 @@ extern "C" int adfft_execute_noalloc(int64_t N, int64_t M, int64_t batch, int dt
     return ADFFT_ERR_UNSUPPORTED_SIZE;
 
   void* base_v = nullptr;
-  int rc = device_setup(&base_v);
+  int dev = 0;
+  int rc = device_setup(&base_v, &dev);
   if (rc != ADFFT_OK) return rc;
   unsigned char* base = static_cast<unsigned char*>(base_v);
   unsigned char* scratch = base + kNoAllocTableBytes;
@@ -269,14 +281,27 @@ extern "C" int adfft_execute_noalloc(int64_t N, int64_t M, int64_t batch, int dt
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = fused_prepare(L1);
   if (e == cudaSuccess) e = twopass_prepare(L2);
-  if (e == cudaSuccess) e = launch_table(base, t1, R1, s);
-  if (e == cudaSuccess) e = launch_table(base, tp, Mc, s);
-  if (e == cudaSuccess) e = launch_table(base, t2, B, s);
-  if (e == cudaSuccess) e = launch_table(base, tm, M, s);
+  {
+    // the tables depend on (R1, Mc, B, M) only: rewrite them when the previous call on
+    // this device used other sizes (calls are serialised on the GPU by contract)
+    const long long key[4] = {(long long)R1, (long long)Mc, (long long)B, (long long)M};
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    const bool same = memcmp(g_table_key[dev], key, sizeof(key)) == 0;
+    if (e == cudaSuccess && !same) {
+      memset(g_table_key[dev], 0, sizeof(key));
+      e = launch_table(base, t1, R1, s);
+      if (e == cudaSuccess) e = launch_table(base, tp, Mc, s);
+      if (e == cudaSuccess) e = launch_table(base, t2, B, s);
+      if (e == cudaSuccess) e = launch_table(base, tm, M, s);
+      if (e == cudaSuccess) memcpy(g_table_key[dev], key, sizeof(key));
+    }
+  }
   if (e == cudaSuccess) e = fused_launch(L1, d_in, scratch, s);
   if (e == cudaSuccess) e = twopass_launch(L2, scratch, d_out, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    memset(g_table_key[dev], 0, sizeof(g_table_key[dev]));
     return ADFFT_ERR_CUDA;
   }
   return ADFFT_OK;

@@ -53,3 +53,18 @@ def test_native_arm_fails_loudly_without_gpu():
     assert r.returncode != 0
     assert r.stdout.strip() == ""          # no JSON line from a run that did not measure
     assert "Error" in r.stderr
+
+
+def test_gpus_flag_launches_that_many_ranks():
+    # --gpus 2 without a torchrun environment relaunches the command as two ranks on a
+    # 127.0.0.1 rendezvous; rank 0 alone prints the line, which counts both ranks
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "2", "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
+
