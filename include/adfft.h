@@ -102,7 +102,8 @@ typedef struct {
     int32_t cluster;      /* CTAs per signal sharing one thread-block cluster */
     int32_t passes;       /* HBM passes per forward transform (1 = fused single pass) */
     double scale;         /* S */
-    int32_t staged;       /* 1 if the fused pass stages each signal through shared memory */
+    int32_t staged;       /* 1 if the fused pass stages each signal through shared memory,
+                             2 if its residues are exchanged by bulk push copies */
     int32_t tuned;        /* 1 if the launch shape came from the autotuner or its cache
                              (ragged plans: every shape class) */
     int32_t grid;         /* clusters the (first) kernel launches; each loops over signals */
@@ -248,7 +249,11 @@ int adfft_plan_autotune(adfft_plan_t plan, const void *d_in, void *d_out, void *
  * fft_len = the sub-FFT length g' (a power of two dividing M and N, halved for
  * real input; 0 = the largest such), cluster = CTAs per signal (0 = the
  * smallest that fits), staged = 1 to stage each signal through shared memory,
- * 0 not to, -1 where it fits; grid = clusters launched: 0 = as many as can be
+ * 0 not to, -1 where it fits, 2 for the push-exchange form (real fp32 input, one
+ * residue per CTA, cluster = the number of residues: each CTA bulk-copies the runs
+ * of its residue that the other CTAs need into their shared memory instead of the
+ * CTAs loading them from one another; served for the compile-time shapes the
+ * library instantiates, ADFFT_ERR_NOT_SUPPORTED otherwise); grid = clusters launched: 0 = as many as can be
  * resident at once, each looping over signals (the default), -1 = one per
  * signal, n > 0 = at most n.  Selects the fold algorithm.  Returns
  * ADFFT_ERR_NOT_SUPPORTED (the plan unchanged) when the shape does not fit

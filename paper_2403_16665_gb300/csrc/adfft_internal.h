@@ -27,6 +27,7 @@ struct FusedLaunch {
   int threads;
   int grid_y;
   size_t smem;
+  bool push = false;   // exchange by bulk push copies (fused_push.cuh) instead of peer loads
 };
 
 // Launch-shape choice of the fused fold path (set by the plan's default rule
@@ -34,7 +35,8 @@ struct FusedLaunch {
 struct FoldChoice {
   int64_t np = 0;    // sub-FFT length: a power of two dividing gcd(Mc, Nc); 0 = the largest such
   int cluster = 0;   // CTAs per cluster; 0 = the smallest that fits
-  int stage = -1;    // input staging through shared memory: 1 required, 0 never, -1 where it fits
+  int stage = -1;    // input staging through shared memory: 1 required, 0 never, -1 where it fits;
+                     // 2: no staging, residues exchanged by bulk push copies (fused_push.cuh)
   int grid = 0;      // clusters launched: 0 = as many as can be resident at once (each loops over
                      // signals), -1 = one per signal, > 0 = that many
 };
@@ -129,6 +131,12 @@ struct Plan {
 using SpecKernel = void (*)(const FusedArgs);
 SpecKernel spec16k_forward(const FusedLaunch& L);
 SpecKernel spec16k_adjoint(const FusedLaunch& L);
+
+// Push-exchange forward kernels (fused_push.cu): the kernel for a launch whose args (C = P,
+// one residue per CTA, packed real fp32, no staging) it serves, else nullptr; and its
+// threads and dynamic shared memory.
+SpecKernel push_forward(const FusedLaunch& L);
+bool push_geometry(const FusedLaunch& L, int* threads, size_t* smem);
 
 // Kernel launchers (fused.cu).  Return a cudaError_t.
 cudaError_t fused_prepare(const FusedLaunch& L);   // sets function attributes once

@@ -109,6 +109,8 @@ std::vector<FoldChoice> fold_candidates(const Plan& p) {
       if (P % c || (P / c) * np > vals) continue;
       for (int st : {1, 0})
         for (int grid : {0, -1}) out.push_back(FoldChoice{np, c, st, grid});
+      // bulk push exchange (one residue per CTA; configure rejects shapes it has no kernel for)
+      if (c == P && !p.dbl && mode == kLoadRealPacked) out.push_back(FoldChoice{np, c, 2, 0});
     }
   }
   return out;
@@ -309,7 +311,7 @@ bool parse_entry(Parser& ps, Key& k, Entry& en) {
   if (!ps.eat('}')) return false;
   if (!have_dev || have != 511) return false;
   if (en.algo != ADFFT_ALGO_FOLD && en.algo != ADFFT_ALGO_FOUR_STEP) return false;
-  if (en.fold.stage != 0 && en.fold.stage != 1) return false;
+  if (en.fold.stage < 0 || en.fold.stage > 2) return false;
   if (en.fold.grid < -1 || en.tp_a < 0) return false;
   return true;
 }
@@ -414,7 +416,7 @@ int adfft_autotune_save(const char* path) {
                "\"algo\": %d, \"fft_len\": %lld, \"cluster\": %d, \"staged\": %d, \"grid\": %d, "
                "\"four_step_a\": %lld, \"ms\": %.6g}",
                (long long)k.N, (long long)k.M, (long long)k.batch, k.dtype, k.precision, e.algo,
-               (long long)e.fold.np, e.fold.cluster, e.fold.stage == 1 ? 1 : 0, e.fold.grid, (long long)e.tp_a,
+               (long long)e.fold.np, e.fold.cluster, e.fold.stage == 2 ? 2 : (e.fold.stage == 1 ? 1 : 0), e.fold.grid, (long long)e.tp_a,
                e.ms);
       o += buf;
     }

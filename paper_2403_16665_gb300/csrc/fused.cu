@@ -40,6 +40,7 @@ bool is_r32_n8192_p8(const FusedLaunch& L, int rpc, int threads) {
 }
 
 KernelFn pick_kernel(const FusedLaunch& L) {
+  if (L.push) return push_forward(L);
   if (is_r32_n8192_p8(L, 2, 512)) return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8>;
   if (KernelFn k = spec16k_forward(L)) return k;
   if (is_r32_n8192_p8(L, 1, 256))
@@ -66,6 +67,7 @@ int fused_values_per_thread(bool dbl) { return dbl ? kVptF64 : kVptF32; }
 
 cudaError_t fused_prepare(const FusedLaunch& L) {
   KernelFn k = pick_kernel(L);
+  if (!k) return cudaErrorInvalidConfiguration;
   // the attribute is per kernel and shared by every plan: always allow the full 227 KiB
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
@@ -78,6 +80,7 @@ cudaError_t fused_prepare(const FusedLaunch& L) {
 
 int fused_max_active_clusters(const FusedLaunch& L) {
   KernelFn k = pick_kernel(L);
+  if (!k) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L.args.C, L.grid_y, 1);
   cfg.blockDim = dim3(L.threads, 1, 1);
@@ -99,6 +102,7 @@ int fused_max_active_clusters(const FusedLaunch& L) {
 
 cudaError_t fused_launch(const FusedLaunch& L, const void* in, void* out, cudaStream_t stream) {
   KernelFn k = pick_kernel(L);
+  if (!k) return cudaErrorInvalidConfiguration;
   FusedArgs a = L.args;
   a.in = in;
   a.out = out;

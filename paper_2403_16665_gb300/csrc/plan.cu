@@ -103,7 +103,8 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   int lo_n, hi_n;
   const int tw_n = (1 << bits) + (int)((Mt + (1 << bits) - 1) >> bits);
   const int64_t region = Np + Np / 16 + 2;
-  const bool can_stage = choice.stage != 0 && stage_bytes > 0 && (stage_bytes % 16) == 0 &&
+  const bool push = choice.stage == 2;   // bulk push exchange: one residue per CTA, no staging
+  const bool can_stage = choice.stage != 0 && !push && stage_bytes > 0 && (stage_bytes % 16) == 0 &&
                          stage_bytes <= (int64_t)kSmemLimit;
   int C = -1, stage = 0;
   size_t smem = 0;
@@ -114,6 +115,7 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
     for (int c = 1; c <= std::min<int64_t>(P, max_cluster); ++c) {
       if (P % c) continue;
       if (choice.cluster > 0 && c != choice.cluster) continue;
+      if (push && c != P) continue;
       const int64_t rpc = P / c;
       if (rpc * Np > max_vals) continue;
       const FusedSmem lay = fused_smem_layout(tw_n, st, (int)rpc, (int)region, (int)esz);
@@ -196,6 +198,19 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   L.threads = threads;
   L.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(batch, 65535));
   L.smem = smem;
+  L.push = false;
+  if (push) {
+    // only the compile-time shapes of fused_push.cu serve this form
+    int pt = 0;
+    size_t ps = 0;
+    L.push = true;
+    if (!push_geometry(L, &pt, &ps) || ps > kSmemLimit) {
+      L.push = false;
+      return ADFFT_ERR_UNSUPPORTED_SIZE;
+    }
+    L.threads = pt;
+    L.smem = ps;
+  }
   cudaError_t e = fused_prepare(L);
   if (e == cudaSuccess) e = adjoint_prepare(L);
   if (e != cudaSuccess) {
@@ -264,7 +279,8 @@ int setup_fold(Plan& p, const FoldChoice* forced) {
   p.fused.args.in_unit = (int)p.in_elem;
   p.fused.args.M = p.M;
   p.fused.args.offs = p.d_offs;
-  p.fold_choice = FoldChoice{p.fused.args.Np, p.fused.args.C, p.fused.args.stage_bytes > 0 ? 1 : 0, ch.grid};
+  p.fold_choice = FoldChoice{p.fused.args.Np, p.fused.args.C,
+                             p.fused.push ? 2 : (p.fused.args.stage_bytes > 0 ? 1 : 0), ch.grid};
   p.fold_ok = true;
   return ADFFT_OK;
 }
@@ -826,7 +842,7 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
 
 int adfft_plan_set_launch_shape(adfft_plan_t plan, int64_t fft_len, int cluster, int staged, int grid) {
   using namespace adfft;
-  if (!plan || fft_len < 0 || cluster < 0 || cluster > kFoldMaxCluster || staged < -1 || staged > 1 || grid < -1)
+  if (!plan || fft_len < 0 || cluster < 0 || cluster > kFoldMaxCluster || staged < -1 || staged > 2 || grid < -1)
     return ADFFT_ERR_INVALID_ARG;
   Plan& p = plan->p;
   if (p.ragged) return ADFFT_ERR_NOT_SUPPORTED;
@@ -902,7 +918,7 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
   }
   info->passes = (p.algo == ADFFT_ALGO_FOUR_STEP) ? 2 : 1;
   info->scale = p.scale;
-  info->staged = (p.algo == ADFFT_ALGO_FOLD && p.fused.args.stage_bytes > 0) ? 1 : 0;
+  info->staged = (p.algo != ADFFT_ALGO_FOLD) ? 0 : p.fused.push ? 2 : (p.fused.args.stage_bytes > 0 ? 1 : 0);
   info->grid = (p.algo == ADFFT_ALGO_FOLD) ? p.fused.grid_y : (p.algo == ADFFT_ALGO_FOUR_STEP) ? p.tp1.grid_y : 0;
   info->tuned = p.tuned ? 1 : 0;
   return ADFFT_OK;
