@@ -195,22 +195,23 @@ __global__ void __launch_bounds__(PS::T, 2) fused_push_kernel(const FusedArgs a)
       // ---- epilogue of half h
       const int A0 = PS::a0(c, h), B0 = PS::b0(c, h);
       const unsigned jb = (unsigned)(PS::JC * c + PS::JH * h + warp * (PS::STEPS * 32));
-      // element of U_r[k] (k inside this half's runs)
-      auto ld_direct = [&](int r, int k) -> V {
-        if (r == c) return buf[SH::pad(k)];
-        const int slot = (r - c - 1 + 2 * P) % P;
-        return land[slot * PS::SLOT + pad32x2(k - A0)];
-      };
-      auto ld_mirror = [&](int r, int k) -> V {
-        if (r == c) return buf[SH::pad(k)];
-        const int slot = (r - c - 1 + 2 * P) % P;
-        return land[slot * PS::SLOT + PS::PADA + pad32x2(k - B0)];
-      };
+      // Per lane the residue r = lane mod P is fixed, so the sources of U_j (residue r, k) and of
+      // U_{Mc-j} (residue rm, k') are fixed too: this CTA's buf when the residue is c, else the
+      // peer's slot in the landing.  Runs start at multiples of 32, so the padded index of k in
+      // either place is base + pad32x2(k - run start); branch-free per lane.
+      const V* sm = reinterpret_cast<const V*>(smem_raw);
+      const int r_l = lane & (P - 1);
+      const int rm_l = (P - r_l) & (P - 1);
+      const int base_d = (r_l == c) ? L.buf / 8 + SH::pad(A0)
+                                    : L.land / 8 + ((r_l - c - 1 + 2 * P) % P) * PS::SLOT;
+      const int base_m = (rm_l == c) ? L.buf / 8 + SH::pad(B0)
+                                     : L.land / 8 + ((rm_l - c - 1 + 2 * P) % P) * PS::SLOT + PS::PADA;
       auto unpack = [&](unsigned j, V& X1, V& X2) {
-        const int r = (int)(j & (P - 1));
         const int k = (int)(j >> PS::LOGP);
-        const V Uj = ld_direct(r, k);
-        const V Up = (r == 0) ? ld_mirror(0, (NP - k) & (NP - 1)) : ld_mirror(P - r, NP - 1 - k);
+        // mirror index: P (Np - 1 - k) + (P - r) for r > 0, P ((Np - k) mod Np) for r = 0
+        const int km = r_l ? NP - 1 - k : (NP - k) & (NP - 1);
+        const V Uj = sm[base_d + pad32x2(k - A0)];
+        const V Up = sm[base_m + pad32x2(km - B0)];
         V wn = tab(j);
         wn = cmake<V>(hS * wn.y, -hS * wn.x);   // (S/2)(-i) W_M^j
         const V A = cadd(Uj, cconj(Up));
