@@ -85,8 +85,10 @@ typedef enum {
 /* Arithmetic form of the length-g FFT stages (adfft_plan_set_precision). */
 typedef enum {
     ADFFT_PREC_NATIVE = 0,     /* FP32 for R32/C64 plans, FP64 for R64/C128 plans */
-    ADFFT_PREC_FP16X2 = 1,     /* tensor-core radix-16 stages, fp16 hi+lo split operands, FP32 accumulate */
-    ADFFT_PREC_BF16X3 = 2      /* tensor-core radix-16 stages, bf16 hi+lo split operands, FP32 accumulate */
+    ADFFT_PREC_FP16X2 = 1,     /* tensor-core radix-16 stages, fp16 hi+lo split operands (3 products),
+                                  FP32 accumulate */
+    ADFFT_PREC_BF16X3 = 2      /* tensor-core radix-16 stages, operands split into three bf16 parts
+                                  (6 products), FP32 accumulate */
 } adfft_precision_t;
 
 /* Read-only description of a plan (adfft_plan_get_info). */

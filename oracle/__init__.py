@@ -56,6 +56,8 @@ def _load():
             lib.oracle_alpha_dft.restype = ctypes.c_int
             lib.oracle_alpha_dft_adjoint.argtypes = [i64, i64, i64, f64, p, p, p, p, ctypes.c_int]
             lib.oracle_alpha_dft_adjoint.restype = ctypes.c_int
+            lib.oracle_alpha_dft_adjoint_samples.argtypes = [i64, i64, i64, f64, p, p, p, i64, p, p, ctypes.c_int]
+            lib.oracle_alpha_dft_adjoint_samples.restype = ctypes.c_int
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -111,12 +113,14 @@ def alpha_dft(x, M: int, S: float | None = None, bins=None, threads: int = 0):
 
 
 def alpha_dft_adjoint(g, N: int, S: float | None = None, real_input: bool = False,
-                      threads: int = 0):
+                      threads: int = 0, samples=None):
     """Conjugate transpose of Eq. 7 times S: xb_n = S sum_m exp(+2 pi i m n/M) g_m.
 
     g: complex array [M] or [batch, M].  For a real-input forward map the
     adjoint with respect to the real inner product is the real part, which is
-    returned when real_input is True.
+    returned when real_input is True.  samples: optional int array of output
+    indices n (0 <= n < N); the result then holds those samples only, in that
+    order ([nsamples] or [batch, nsamples]).
     """
     g = np.asarray(g)
     one = g.ndim == 1
@@ -125,10 +129,19 @@ def alpha_dft_adjoint(g, N: int, S: float | None = None, real_input: bool = Fals
     S = (1.0 / N) if S is None else float(S)
     gr = np.ascontiguousarray(g2.real, dtype=np.float64)
     gi = np.ascontiguousarray(g2.imag, dtype=np.float64)
-    xr = np.empty((B, N), dtype=np.float64)
-    xi = np.empty((B, N), dtype=np.float64)
-    rc = _load().oracle_alpha_dft_adjoint(B, int(N), M, S, _ptr(gr), _ptr(gi), _ptr(xr),
-                                          _ptr(xi), int(threads))
+    if samples is not None:
+        smp = np.ascontiguousarray(np.asarray(samples, dtype=np.int64))
+        if smp.size and (smp.min() < 0 or smp.max() >= N):
+            raise ValueError("sample index out of range")
+        xr = np.empty((B, smp.size), dtype=np.float64)
+        xi = np.empty((B, smp.size), dtype=np.float64)
+        rc = _load().oracle_alpha_dft_adjoint_samples(B, int(N), M, S, _ptr(gr), _ptr(gi), _ptr(smp),
+                                                      int(smp.size), _ptr(xr), _ptr(xi), int(threads))
+    else:
+        xr = np.empty((B, N), dtype=np.float64)
+        xi = np.empty((B, N), dtype=np.float64)
+        rc = _load().oracle_alpha_dft_adjoint(B, int(N), M, S, _ptr(gr), _ptr(gi), _ptr(xr),
+                                              _ptr(xi), int(threads))
     if rc != 0:
         raise ValueError("oracle_alpha_dft_adjoint rejected its arguments")
     out = xr if real_input else xr + 1j * xi

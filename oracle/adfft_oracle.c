@@ -107,6 +107,25 @@ int oracle_alpha_dft(int64_t batch, int64_t N, int64_t M, double S,
     return 0;
 }
 
+/* One output sample of the adjoint: S * sum_m conj(W_M^{mn}) g_m for signal row gr, gi. */
+static void adjoint_sample(int64_t N, int64_t M, double S, const double *gr, const double *gi,
+                           int64_t n, double *out_re, double *out_im) {
+    (void)N;
+    acc_t re = {0.0, 0.0}, im = {0.0, 0.0};
+    int64_t j = 0;                          /* (m*n) mod M, exact */
+    int64_t step = n % M;
+    for (int64_t m = 0; m < M; ++m) {
+        double c, s;
+        unit_root(j, M, +1, &c, &s);        /* conj(W_M^{mn}) */
+        acc_add(&re, gr[m] * c - gi[m] * s);
+        acc_add(&im, gr[m] * s + gi[m] * c);
+        j += step;
+        if (j >= M) j -= M;
+    }
+    *out_re = S * acc_get(&re);
+    *out_im = S * acc_get(&im);
+}
+
 /*
  * Adjoint transform (conjugate transpose of the Eq. 7 matrix, times S).
  *   g_re, g_im : [batch][M] (all M bins in natural order).
@@ -125,20 +144,34 @@ int oracle_alpha_dft_adjoint(int64_t batch, int64_t N, int64_t M, double S,
     #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < total; ++t) {
         int64_t b = t / N, n = t % N;
-        const double *gr = g_re + b * M, *gi = g_im + b * M;
-        acc_t re = {0.0, 0.0}, im = {0.0, 0.0};
-        int64_t j = 0;                          /* (m*n) mod M, exact */
-        int64_t step = n % M;
-        for (int64_t m = 0; m < M; ++m) {
-            double c, s;
-            unit_root(j, M, +1, &c, &s);        /* conj(W_M^{mn}) */
-            acc_add(&re, gr[m] * c - gi[m] * s);
-            acc_add(&im, gr[m] * s + gi[m] * c);
-            j += step;
-            if (j >= M) j -= M;
-        }
-        xb_re[t] = S * acc_get(&re);
-        xb_im[t] = S * acc_get(&im);
+        adjoint_sample(N, M, S, g_re + b * M, g_im + b * M, n, &xb_re[t], &xb_im[t]);
+    }
+    return 0;
+}
+
+/*
+ * The same adjoint at chosen output samples only (for transforms whose full
+ * adjoint would take too long): xb[b][q] = sample samples[q] (0 <= samples[q] < N)
+ * of signal b.  Same arithmetic per sample as oracle_alpha_dft_adjoint.
+ *   xb_re, xb_im : [batch][nsamples] outputs.
+ */
+int oracle_alpha_dft_adjoint_samples(int64_t batch, int64_t N, int64_t M, double S,
+                                     const double *g_re, const double *g_im,
+                                     const int64_t *samples, int64_t nsamples,
+                                     double *xb_re, double *xb_im, int nthreads) {
+    if (batch < 0 || N < 1 || M < 1 || nsamples < 0 || (nsamples > 0 && samples == NULL)) return -1;
+    for (int64_t q = 0; q < nsamples; ++q)
+        if (samples[q] < 0 || samples[q] >= N) return -1;
+    int64_t total = batch * nsamples;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < total; ++t) {
+        int64_t b = t / nsamples, q = t % nsamples;
+        adjoint_sample(N, M, S, g_re + b * M, g_im + b * M, samples[q], &xb_re[t], &xb_im[t]);
     }
     return 0;
 }

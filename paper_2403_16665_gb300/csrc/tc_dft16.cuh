@@ -5,12 +5,15 @@
 //     F = [[ C, -S ], [ S, C ]] with C_kn = cos(2 pi k n/16), S_kn = sin(2 pi k n/16),
 //
 // for tiles of 16 vectors (one warp, mma.sync m16n8k16, FP32 accumulation).
-// Operands are split into a 16-bit high part and a 16-bit low part
-// (x = hi + lo), and the product is formed as hi.hi + hi.lo + lo.hi, which
-// recovers about 22 bits (fp16) or 16 bits (bf16) of each operand.  Each tile
-// is scaled by a power of two so that its largest input lies in [2^14, 2^15)
-// before the split (fp16 range), and unscaled after the product.  Stage
-// twiddles are applied in FP32 before the split, from the FP64-derived table.
+// FP16X2: operands split into a high and a low fp16 part (x = hi + lo, 22
+// significand bits), product hi.hi + hi.lo + lo.hi (3 MMAs).
+// BF16X3: operands split into three bf16 parts (x = x0 + x1 + x2, 24 bits),
+// product x0.y0 + x0.y1 + x1.y0 + x0.y2 + x1.y1 + x2.y0 (6 MMAs): every term of
+// order below 2^-24 relative is dropped, so both forms carry FP32 accuracy.
+// Each tile is scaled by a power of two so that its largest input lies in
+// [2^14, 2^15) before the split (fp16 range), and unscaled after the product.
+// Stage twiddles are applied in FP32 before the split, from the FP64-derived
+// table.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -46,6 +49,24 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
   hi = pack2<PREC>(a, b);
   const float2 h = unpack2<PREC>(hi);
   lo = pack2<PREC>(a - h.x, b - h.y);
+}
+// x0 = round(x), x1 = round(x - x0), x2 = round(x - x0 - x1) (each subtraction exact in FP32).
+template <int PREC>
+__device__ __forceinline__ void split3(float a, float b, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
+  p0 = pack2<PREC>(a, b);
+  const float2 h0 = unpack2<PREC>(p0);
+  const float ra = a - h0.x, rb = b - h0.y;
+  p1 = pack2<PREC>(ra, rb);
+  const float2 h1 = unpack2<PREC>(p1);
+  p2 = pack2<PREC>(ra - h1.x, rb - h1.y);
+}
+// Split of an operand pair into the parts the form multiplies: [0] high, [1] low (FP16X2) or
+// [0] x0, [1] x1, [2] x2 (BF16X3).
+template <int PREC> struct Parts { static constexpr int n = (PREC == 2) ? 3 : 2; };
+template <int PREC>
+__device__ __forceinline__ void split_parts(float a, float b, uint32_t (&p)[Parts<PREC>::n]) {
+  if constexpr (Parts<PREC>::n == 3) split3<PREC>(a, b, p[0], p[1], p[2]);
+  else split2<PREC>(a, b, p[0], p[1]);
 }
 
 template <int PREC>
@@ -86,18 +107,24 @@ __device__ __forceinline__ float dft16_real_entry(int k, int n) {
   return c;                        // Im v -> Im y :  cos
 }
 
-// B fragments (hi and lo) of F for this lane: [kstep 2][ntile 4][2 regs].
+// B fragments of F for this lane, split into parts: [part][kstep 2][ntile 4][2 regs].
 template <int PREC>
-__device__ __forceinline__ void load_dft16_fragments(uint32_t (&bhi)[2][4][2], uint32_t (&blo)[2][4][2]) {
+__device__ __forceinline__ void load_dft16_fragments(uint32_t (&bp)[Parts<PREC>::n][2][4][2]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  constexpr int NP = Parts<PREC>::n;
 #pragma unroll
   for (int ks = 0; ks < 2; ++ks) {
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       const int n = 8 * nt + g;
       const int k0 = 16 * ks + 2 * t;
-      split2<PREC>(dft16_real_entry(k0, n), dft16_real_entry(k0 + 1, n), bhi[ks][nt][0], blo[ks][nt][0]);
-      split2<PREC>(dft16_real_entry(k0 + 8, n), dft16_real_entry(k0 + 9, n), bhi[ks][nt][1], blo[ks][nt][1]);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        uint32_t q[NP];
+        split_parts<PREC>(dft16_real_entry(k0 + 8 * r, n), dft16_real_entry(k0 + 8 * r + 1, n), q);
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) bp[pp][ks][nt][r] = q[pp];
+      }
     }
   }
 }
@@ -119,8 +146,9 @@ __device__ void stockham_pass_tc(const FusedArgs& a, V* buf, const TwTable<V>& t
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const unsigned tw_step = (unsigned)a.Mt / ((unsigned)Ns << 4);
   const int in_step = items_res + (items_res >> 4);       // pad16(j + i S) = pad16(j) + i (S + S/16)
-  uint32_t bhi[2][4][2], blo[2][4][2];
-  load_dft16_fragments<PREC>(bhi, blo);
+  constexpr int NPART = Parts<PREC>::n;
+  uint32_t bp[NPART][2][4][2];
+  load_dft16_fragments<PREC>(bp);
   // element slot e -> DFT index i
   const int idx4[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
   float2 res[TPT][2][4];                                  // [tile][row g / g+8][slot]
@@ -165,7 +193,7 @@ __device__ void stockham_pass_tc(const FusedArgs& a, V* buf, const TwTable<V>& t
     const float up = __int_as_float((127 + 14 - ex) << 23);     // 2^(14 - ex)
     const float down = __int_as_float((127 - 14 + ex) << 23);   // 2^(ex - 14)
     // A fragments: kstep 0 = real parts, kstep 1 = imaginary parts
-    uint32_t ahi[2][4], alo[2][4];
+    uint32_t ap[NPART][2][4];
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
       // a0:(g, 2t..2t+1) a1:(g+8, 2t..) a2:(g, 2t+8..) a3:(g+8, 2t+8..)
@@ -173,10 +201,14 @@ __device__ void stockham_pass_tc(const FusedArgs& a, V* buf, const TwTable<V>& t
       const float p10 = (ks ? x[1][0].y : x[1][0].x) * up, p11 = (ks ? x[1][1].y : x[1][1].x) * up;
       const float p02 = (ks ? x[0][2].y : x[0][2].x) * up, p03 = (ks ? x[0][3].y : x[0][3].x) * up;
       const float p12 = (ks ? x[1][2].y : x[1][2].x) * up, p13 = (ks ? x[1][3].y : x[1][3].x) * up;
-      split2<PREC>(p00, p01, ahi[ks][0], alo[ks][0]);
-      split2<PREC>(p10, p11, ahi[ks][1], alo[ks][1]);
-      split2<PREC>(p02, p03, ahi[ks][2], alo[ks][2]);
-      split2<PREC>(p12, p13, ahi[ks][3], alo[ks][3]);
+      const float pv[4][2] = {{p00, p01}, {p10, p11}, {p02, p03}, {p12, p13}};
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        uint32_t q[NPART];
+        split_parts<PREC>(pv[f][0], pv[f][1], q);
+#pragma unroll
+        for (int pp = 0; pp < NPART; ++pp) ap[pp][ks][f] = q[pp];
+      }
     }
     float d[4][4];
 #pragma unroll
@@ -185,9 +217,15 @@ __device__ void stockham_pass_tc(const FusedArgs& a, V* buf, const TwTable<V>& t
       for (int q = 0; q < 4; ++q) d[nt][q] = 0.f;
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
-        mma16816<PREC>(d[nt], ahi[ks], bhi[ks][nt]);
-        mma16816<PREC>(d[nt], ahi[ks], blo[ks][nt]);
-        mma16816<PREC>(d[nt], alo[ks], bhi[ks][nt]);
+        // smallest terms first: the FP32 accumulator adds them before the dominant product
+        if constexpr (NPART == 3) {
+          mma16816<PREC>(d[nt], ap[2][ks], bp[0][ks][nt]);
+          mma16816<PREC>(d[nt], ap[1][ks], bp[1][ks][nt]);
+          mma16816<PREC>(d[nt], ap[0][ks], bp[2][ks][nt]);
+        }
+        mma16816<PREC>(d[nt], ap[1][ks], bp[0][ks][nt]);
+        mma16816<PREC>(d[nt], ap[0][ks], bp[1][ks][nt]);
+        mma16816<PREC>(d[nt], ap[0][ks], bp[0][ks][nt]);
       }
     }
     // D fragment (row g: d[.][0..1], row g+8: d[.][2..3]) at columns 8 nt + 2t + {0,1}:

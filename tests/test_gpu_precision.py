@@ -1,8 +1,9 @@
-"""Precision forms: radix-16 stages on the tensor cores with split (hi + lo)
-fp16 or bf16 operands and FP32 accumulation, against the FP64 oracle.  The
-error of every form is printed (pytest -s) and checked against a bound:
-FP16X2 must meet the FP32 tolerance 2e-6 * log2(M); BF16X3 keeps ~16
-significand bits per operand and is held to 1e-4 * log2(M)."""
+"""Precision forms: radix-16 stages on the tensor cores with split operands and
+FP32 accumulation (FP16X2: fp16 hi + lo, 3 products; BF16X3: three bf16 parts, 6
+products), against the FP64 oracle.  Every form is held to the FP32 tolerance
+2e-6 * log2(M), overall and in every bin range of the large workload (windows
+around the tones by amplitude decade, and the noise floor), for every signal
+checked.  The errors are printed (pytest -s)."""
 import numpy as np
 import pytest
 
@@ -20,7 +21,7 @@ def _torch():
     return torch
 
 
-BOUND = {adfft.PREC_NATIVE: 2e-6, adfft.PREC_FP16X2: 2e-6, adfft.PREC_BF16X3: 1e-4}
+BOUND = {adfft.PREC_NATIVE: 2e-6, adfft.PREC_FP16X2: 2e-6, adfft.PREC_BF16X3: 2e-6}
 
 
 def run(torch, x_np, M, code, prec):
@@ -74,27 +75,32 @@ def test_large_precision_workload_per_bin_range(prec):
     N, M = 1 << 22, 1 << 26
     X, plan = run(torch, x, M, adfft.R32, prec)
     rng = np.random.default_rng(4)
-    s = 0
-    A, nu = prm["A"][s], prm["nu"][s]
-    groups = {}
-    for a_lo in (1e-4, 1e-3, 1e-2, 1e-1):
-        sel = (A >= a_lo) & (A < 10 * a_lo)
-        if not sel.any():
-            continue
-        centers = np.round(nu[sel] * 16).astype(np.int64)
-        win = (centers[:, None] + np.arange(-32, 33)[None, :]).ravel() % M
-        groups["tones %.0e..%.0e" % (a_lo, 10 * a_lo)] = np.unique(win)
-    groups["noise floor"] = np.unique(rng.integers(0, M, 400))
-    allbins = np.unique(np.concatenate(list(groups.values())))
-    got_all = X[s, torch.from_numpy(allbins).cuda()].cpu().numpy()
-    ref_all = oracle.alpha_dft(x[s].astype(np.float64), M, bins=allbins)
-    pos = {b: i for i, b in enumerate(allbins)}
-    report = []
-    for name, b in groups.items():
-        idx = np.array([pos[v] for v in b])
-        e = np.linalg.norm(got_all[idx] - ref_all[idx]) / np.linalg.norm(ref_all[idx])
-        report.append("%s: %.2e" % (name, e))
-    overall = np.linalg.norm(got_all - ref_all) / np.linalg.norm(ref_all)
-    print("precision %d, N=2^22 alpha=16, rel-RMS overall %.2e; %s" % (prec, overall, "; ".join(report)))
-    assert np.isfinite(got_all).all()
-    assert overall <= BOUND[prec] * np.log2(M)
+    tol = BOUND[prec] * np.log2(M)
+    for s in range(x.shape[0]):
+        A, nu = prm["A"][s], prm["nu"][s]
+        groups = {}
+        for a_lo in (1e-4, 1e-3, 1e-2, 1e-1):
+            sel = (A >= a_lo) & (A < 10 * a_lo)
+            if not sel.any():
+                continue
+            centers = np.round(nu[sel] * 16).astype(np.int64)
+            win = (centers[:, None] + np.arange(-32, 33)[None, :]).ravel() % M
+            groups["tones %.0e..%.0e" % (a_lo, 10 * a_lo)] = np.unique(win)
+        groups["noise floor"] = np.unique(rng.integers(0, M, 400))
+        allbins = np.unique(np.concatenate(list(groups.values())))
+        got_all = X[s, torch.from_numpy(allbins).cuda()].cpu().numpy()
+        ref_all = oracle.alpha_dft(x[s].astype(np.float64), M, bins=allbins)
+        pos = {b: i for i, b in enumerate(allbins)}
+        report, errs = [], {}
+        for name, b in groups.items():
+            idx = np.array([pos[v] for v in b])
+            e = np.linalg.norm(got_all[idx] - ref_all[idx]) / np.linalg.norm(ref_all[idx])
+            errs[name] = e
+            report.append("%s: %.2e" % (name, e))
+        overall = np.linalg.norm(got_all - ref_all) / np.linalg.norm(ref_all)
+        print("precision %d, N=2^22 alpha=16, signal %d, rel-RMS overall %.2e; %s"
+              % (prec, s, overall, "; ".join(report)))
+        assert np.isfinite(got_all).all()
+        assert overall <= tol, (s, overall)
+        for name, e in errs.items():
+            assert e <= tol, (s, name, e)

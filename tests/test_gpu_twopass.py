@@ -163,3 +163,32 @@ def test_two_pass_adjoint_dot_product(code, N, alpha, four_step):
     if real:
         lhs, rhs = lhs.real, rhs.real
     assert abs((lhs - rhs).item()) <= 5e-6 * max(1.0, abs(lhs.item())) * np.sqrt(np.log2(M))
+
+
+@pytest.mark.parametrize("code,N,alpha,batch", [(adfft.R32, 1 << 22, 16, 2), (adfft.R32, 1 << 17, 8, 3),
+                                                (adfft.C64, 1 << 16, 16, 2)])
+def test_two_pass_fp32_adjoint_elementwise(code, N, alpha, batch):
+    """FP32 two-pass adjoint element by element against the oracle's explicit adjoint, at
+    sampled output samples (first, last, column and block boundaries of the four-step split,
+    random) of every signal, including the 2^22-sample, alpha = 16 workload."""
+    torch = _torch()
+    M = int(round(alpha * N))
+    real = code == adfft.R32
+    rng = np.random.default_rng(N + batch)
+    g = (rng.standard_normal((batch, M)) + 1j * rng.standard_normal((batch, M))).astype(np.complex64)
+    dev = torch.device("cuda:0")
+    plan = adfft.Plan(N, batch=batch, dtype=code, M=M)
+    plan.set_algorithm(adfft.ALGO_FOUR_STEP)
+    info = plan.info
+    assert info.passes == 2
+    gt = torch.from_numpy(g).to(dev)
+    xb = torch.empty((batch, N), dtype=torch.float32 if real else torch.complex64, device=dev)
+    plan.execute_adjoint(gt.data_ptr(), xb.data_ptr())
+    plan.sync_status()
+    A = info.four_step_a
+    edges = [0, 1, N - 1, N // 2, A - 1, A, N - A, 2 * A + 1]
+    samples = np.unique(np.concatenate([np.array(edges) % N, rng.integers(0, N, 24)]))
+    got = xb[:, torch.from_numpy(samples).to(dev)].cpu().numpy()
+    ref = oracle.alpha_dft_adjoint(g.astype(np.complex128), N, real_input=real, samples=samples)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= tol_for(M, False), err

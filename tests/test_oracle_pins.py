@@ -214,6 +214,25 @@ def test_adjoint_against_direct_matrix():
     assert _rel(gr, np.real(A.conj().T @ g)) < 1e-14
 
 
+@pytest.mark.parametrize("N,M", [(12, 30), (64, 256), (50, 20)])
+def test_sampled_adjoint_equals_full_adjoint(N, M):
+    """The sampled-output adjoint evaluates the same sums as the full adjoint at the chosen
+    samples (bit for bit), in the order given, for one and several signals; and, independently,
+    the explicit conjugate-transposed matrix of Eq. 7 at those samples."""
+    rng = np.random.default_rng(N + M)
+    g = _rand(M) if N % 2 else np.stack([_rand(M) for _ in range(3)])
+    samples = rng.permutation(N)[: max(1, N // 3)]
+    full = oracle.alpha_dft_adjoint(g, N)
+    part = oracle.alpha_dft_adjoint(g, N, samples=samples)
+    assert np.array_equal(part, full[..., samples])
+    A = np.exp(-2j * np.pi * np.outer(np.arange(M), samples) / M) / N
+    assert _rel(part, (A.conj().T @ np.atleast_2d(g).T).T.reshape(part.shape)) < 1e-13
+    assert np.array_equal(oracle.alpha_dft_adjoint(g, N, real_input=True, samples=samples),
+                          np.real(full[..., samples]))
+    with pytest.raises(ValueError):
+        oracle.alpha_dft_adjoint(g, N, samples=[N])
+
+
 @pytest.mark.parametrize("N,M", [(12, 8), (40, 10), (9, 6)])
 def test_alpha_below_one_aliasing(N, M):
     """Sec. 2, alpha < 1: reconstruction through Eq. 8 folds the signal,
