@@ -296,6 +296,12 @@ def run_native(args):
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                "sample": "%d bins of 4 signals of the same workload, FP64 direct sum, %.1f s" % (pts, secs)}
 
+    context = None
+    if rank == 0 and not args.no_context:
+        # the other configurations and cuFFT on zero-padded input, same GPU, outside the timed region
+        from paper_2403_16665_gb300 import compare
+        context = compare.context(dev)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -315,6 +321,7 @@ def run_native(args):
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": args.steps * info.passes,
+            "context": context,
         }
         print(json.dumps(line), flush=True)
     plan.destroy()
@@ -348,6 +355,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true", help="keep the plan's default launch shape")
+    ap.add_argument("--no-context", action="store_true",
+                    help="skip the same-GPU measurements of the other configurations and of cuFFT")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -36,6 +36,15 @@
  *     still yields all M bins.  Device pointers must be 16-byte aligned.
  *   - Every call returns ADFFT_OK (0) or a negative adfft_status; a call that
  *     fails launches nothing.  No C++ exception crosses this interface.
+ *   - Failure injection for tests: the environment variable ADFFT_FAULT, read
+ *     when a plan is created, makes that plan fail on purpose (unset: no
+ *     effect).  "alloc:<k>": the k-th device allocation of the creation fails
+ *     (the creation returns NULL, adfft_last_error() = ADFFT_ERR_OOM, nothing
+ *     stays allocated); "launch": every launch of the plan fails (the calls
+ *     return ADFFT_ERR_CUDA and launch nothing); "copy_skip:<s>": the fused
+ *     kernel does not issue the input copy of signal s and gives up waiting for
+ *     it after ~10 ms, so adfft_plan_sync_status reports ADFFT_ERR_TIMEOUT (the
+ *     cluster concerned transforms no later signal; nothing faults or hangs).
  */
 #ifndef ADFFT_H
 #define ADFFT_H

@@ -61,7 +61,17 @@ struct TwoPassLaunch {
   size_t smem;
 };
 
+// Test fault injection requested through ADFFT_FAULT (plan.cu).
+struct FaultSpec {
+  int alloc_at = 0;          // fail the k-th device allocation of plan creation (0: none)
+  bool launch = false;       // every launch of the plan fails without launching
+  long long copy_skip = -1;  // the fused kernel skips the input copy of this signal (-1: none)
+};
+FaultSpec read_fault_spec();
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 struct Plan {
+  FaultSpec fault{};
   int64_t N = 0, M = 0, batch = 0;
   int dtype = 0;
   bool real = false, dbl = false;

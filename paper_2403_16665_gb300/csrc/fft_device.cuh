@@ -188,10 +188,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
 }
 // Wait for phase `phase` of `bar` to complete, giving up after ~2 s of SM clock.
 constexpr long long kWaitLimitCycles = 4000000000ll;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
+                                                  long long limit = kWaitLimitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, phase)) {
-    if (clock64() - t0 > kWaitLimitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }

@@ -70,6 +70,10 @@ struct FusedArgs {
   const void* post_tw;
   int post_bits, post_lo_n;
   long long Mpost;
+  // fault injection for tests (0 = none): the input copy of signal fault_sig1 - 1 is not issued,
+  // and waits on input copies give up after wait_limit cycles instead of the default (~2 s)
+  long long fault_sig1;
+  long long wait_limit;
 };
 
 // Compile-time shape of a specialised instantiation; a zero field is read from
@@ -426,21 +430,26 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   uint32_t phase = 0, fail_phase = 0;
   bool failed = false;
 
+  const long long wait_limit = a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles;
   // prefetch the first signal's input
   if (staged && threadIdx.x == 0 && (long long)blockIdx.y < a.batch) {
     mbar_arrive_expect_tx(bar, (uint32_t)a.stage_bytes);
-    bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, blockIdx.y),
-                  (uint32_t)a.stage_bytes, bar);
+    if ((long long)blockIdx.y + 1 != a.fault_sig1)
+      bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, blockIdx.y),
+                    (uint32_t)a.stage_bytes, bar);
   }
 
   for (long long sig = blockIdx.y; sig < a.batch; sig += gridDim.y) {
     const void* u;
     if (staged) {
       u = stage;
-      if (!failed && !mbar_wait_bounded(bar, phase)) {
+      // the CTA decides as one: after a wait ran out it transforms no further signal (it keeps
+      // taking part in the cluster barriers, so its peers are not left waiting)
+      const bool ok = failed || mbar_wait_bounded(bar, phase, wait_limit);
+      if (__syncthreads_or(!ok) && !failed) {
         failed = true;
         fail_phase = phase;
-        if (a.status) atomicExch(a.status, kStatusTimeout);
+        if (threadIdx.x == 0 && a.status) atomicExch(a.status, kStatusTimeout);
       }
       phase ^= 1u;
     } else if (MODE == kColumns) {
@@ -454,8 +463,10 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 
     // ---- K1: fold + residue twiddle + first radix
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
-    if (staged) first_pass<R0, V, true, SH>(a, u, reinterpret_cast<const V*>(stage), MODE, buf, tab, r0);
-    else first_pass<R0, V, false, SH>(a, u, nullptr, MODE, buf, tab, r0);
+    if (!failed) {
+      if (staged) first_pass<R0, V, true, SH>(a, u, reinterpret_cast<const V*>(stage), MODE, buf, tab, r0);
+      else first_pass<R0, V, false, SH>(a, u, nullptr, MODE, buf, tab, r0);
+    }
     __syncthreads();
 
     // prefetch the next signal's input while this one is transformed
@@ -463,13 +474,16 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     if (staged && threadIdx.x == 0 && nxt < a.batch && !failed) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(bar, (uint32_t)a.stage_bytes);
-      bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, nxt),
-                    (uint32_t)a.stage_bytes, bar);
+      if (nxt + 1 != a.fault_sig1)
+        bulk_copy_g2s(stage, reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, nxt),
+                      (uint32_t)a.stage_bytes, bar);
     }
 
     // ---- K2: radix-16 Stockham passes in shared memory
     int Ns = R0, logNs = LOGR0;
-    if constexpr (SH::fixed) {
+    if (failed) {
+      // no transform after a failed wait: only the cluster barriers below
+    } else if constexpr (SH::fixed) {
       constexpr int kPasses = SH_PASSES<SH, LOGR0>::value;
 #pragma unroll
       for (int p = 1; p < kPasses; ++p) {
@@ -487,7 +501,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 
     // ---- K3: interleave epilogue through distributed shared memory
     if (a.C > 1) { cluster_arrive(); cluster_wait(); } else { __syncthreads(); }
-    if (lane_ok) {
+    if (lane_ok && !failed) {
       if constexpr (KG == 2) {
         // pairs of k: thread (r_l, kq) handles k = 2 kq and 2 kq + 1 of residue r_l, i.e. bins
         // j0 = 2 kq P + r_l and j1 = j0 + P; U[k], U[k+1] come in one 16-byte load, and so do
@@ -632,7 +646,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   }
   if (a.C > 1 && (long long)blockIdx.y < a.batch) cluster_wait();
   // a copy can only still be in flight after a timed-out wait: give it time to land
-  if (failed && threadIdx.x == 0) mbar_wait_bounded(bar, fail_phase);
+  if (failed && threadIdx.x == 0) mbar_wait_bounded(bar, fail_phase, wait_limit);
 }
 
 }  // namespace adfft

@@ -1,6 +1,7 @@
 // Host side of the adfft C ABI: plan validation, algorithm and launch-shape
 // selection, FP64-derived tables, and the extern "C" entry points.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -11,6 +12,36 @@
 #include "adfft_internal.h"
 
 namespace adfft {
+
+// ---- fault injection for tests (environment variable ADFFT_FAULT, read at plan creation) ----
+//   alloc:<k>      the k-th device allocation of the plan creation (k >= 1) fails as out of memory
+//   launch         every launch of the plan's kernels fails (ADFFT_ERR_CUDA, nothing launched)
+//   copy_skip:<s>  the fused kernel does not issue the input copy of signal s and gives up
+//                  waiting for it after ~10 ms: the plan then reports ADFFT_ERR_TIMEOUT
+// Unset (the normal case): no effect.
+namespace {
+thread_local int g_alloc_count = 0;     // device allocations of the plan creation under way
+thread_local int g_alloc_fail_at = 0;   // the one that fails (0: none)
+}  // namespace
+
+FaultSpec read_fault_spec() {
+  FaultSpec f;
+  const char* v = getenv("ADFFT_FAULT");
+  if (!v || !*v) return f;
+  if (strncmp(v, "alloc:", 6) == 0) f.alloc_at = atoi(v + 6);
+  else if (strcmp(v, "launch") == 0) f.launch = true;
+  else if (strncmp(v, "copy_skip:", 10) == 0) f.copy_skip = atoll(v + 10);
+  return f;
+}
+
+// cudaMalloc through the allocation fault hook.
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (g_alloc_fail_at > 0 && ++g_alloc_count == g_alloc_fail_at) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
 
 namespace {
 
@@ -177,7 +208,7 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
       tw_bytes = t.size() * sizeof(float);
       host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + tw_bytes);
     }
-    cudaError_t e = cudaMalloc(d_tw, tw_bytes);
+    cudaError_t e = dev_malloc(d_tw, tw_bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       *d_tw = nullptr;
@@ -279,6 +310,10 @@ int setup_fold(Plan& p, const FoldChoice* forced) {
   p.fused.args.in_unit = (int)p.in_elem;
   p.fused.args.M = p.M;
   p.fused.args.offs = p.d_offs;
+  if (p.fault.copy_skip >= 0) {
+    p.fused.args.fault_sig1 = p.fault.copy_skip + 1;
+    p.fused.args.wait_limit = 20000000;   // ~10 ms of SM clock
+  }
   p.fold_choice = FoldChoice{p.fused.args.Np, p.fused.args.C,
                              p.fused.push ? 2 : (p.fused.args.stage_bytes > 0 ? 1 : 0), ch.grid};
   p.fold_ok = true;
@@ -404,7 +439,7 @@ int setup_twopass(Plan& p) {
       // scratch [batch][B][R1]
       p.ws_bytes = (size_t)p.batch * (size_t)Mc * esz;
       if (p.ws_bytes) {
-        e = cudaMalloc(&p.d_ws, p.ws_bytes);
+        e = dev_malloc(&p.d_ws, p.ws_bytes);
         if (e != cudaSuccess) {
           cudaGetLastError();
           p.d_ws = nullptr;
@@ -473,7 +508,7 @@ std::complex<double> chirp(int64_t j, int64_t M) {
 template <typename T>
 int upload(void** dst, const std::vector<T>& v) {
   const size_t bytes = v.size() * sizeof(T);
-  cudaError_t e = cudaMalloc(dst, bytes);
+  cudaError_t e = dev_malloc(dst, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *dst = nullptr;
@@ -592,6 +627,7 @@ int setup_bluestein(Plan& p) {
 int cuda_status_of(cudaError_t e) { return cuda_status(e); }
 
 int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s) {
+  if (p.fault.launch) return ADFFT_ERR_CUDA;   // injected launch failure: nothing is launched
   cudaError_t e;
   const bool tc = p.precision != ADFFT_PREC_NATIVE;
   const bool f16 = p.precision == ADFFT_PREC_FP16X2;
@@ -617,6 +653,7 @@ int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s) {
 }
 
 int launch_adjoint(Plan& p, const void* g, void* xb, cudaStream_t s) {
+  if (p.fault.launch) return ADFFT_ERR_CUDA;
   cudaError_t e;
   // the selected fold form, else whichever fold form the plan has (the chirp-z form has no adjoint kernel)
   const bool use_tp = p.tp_ok && (p.algo == ADFFT_ALGO_FOUR_STEP || !p.fold_ok);
@@ -723,12 +760,18 @@ adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dty
   p.in_elem = p.real ? (p.dbl ? 8 : 4) : (p.dbl ? 16 : 8);
   p.out_elem = p.dbl ? 16 : 8;
   p.scale = 1.0 / (double)N;
+  p.fault = read_fault_spec();
+  g_alloc_count = 0;
+  g_alloc_fail_at = p.fault.alloc_at;
+  struct Disarm {
+    ~Disarm() { g_alloc_fail_at = 0; }
+  } disarm;
   if (cudaGetDevice(&p.device) != cudaSuccess) {
     cudaGetLastError();
     return fail(ADFFT_ERR_CUDA, h);
   }
   {
-    cudaError_t e = cudaMalloc(&p.d_status, sizeof(int));
+    cudaError_t e = dev_malloc(reinterpret_cast<void**>(&p.d_status), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
       cudaGetLastError();
