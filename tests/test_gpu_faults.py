@@ -37,22 +37,25 @@ def fault_env(monkeypatch):
     monkeypatch.delenv("ADFFT_FAULT", raising=False)
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
-def test_allocation_fault_reports_oom_and_frees(fault_env, k):
+# (N, M, batch, k): the single-pass plan allocates its status word and twiddle table; the
+# two-pass plan (N = 2^22, alpha = 16) also its pass tables and a 256 MiB workspace (the 6th)
+@pytest.mark.parametrize("n,m,batch,k", [(N, M, 64, 1), (N, M, 64, 2), (1 << 22, 1 << 26, 1, 3),
+                                         (1 << 22, 1 << 26, 1, 6)])
+def test_allocation_fault_reports_oom_and_frees(fault_env, n, m, batch, k):
     torch = _torch()
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     fault_env("alloc:%d" % k)
     with pytest.raises(adfft.AdfftError) as ei:
-        adfft.Plan(N, batch=64, dtype=adfft.R32, M=M)
+        adfft.Plan(n, batch=batch, dtype=adfft.R32, M=m)
     assert ei.value.code == -7              # ADFFT_ERR_OOM
     assert adfft.load().adfft_last_error() == -7
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
     assert abs(free1 - free0) <= (8 << 20)  # nothing of the failed creation stays allocated
     fault_env("")
-    p = adfft.Plan(N, batch=64, dtype=adfft.R32, M=M)
-    assert p.info.M == M
+    p = adfft.Plan(n, batch=batch, dtype=adfft.R32, M=m)
+    assert p.info.M == m
 
 
 def test_launch_fault_launches_nothing(fault_env):
