@@ -63,7 +63,7 @@ def test_launch_fault_launches_nothing(fault_env):
     fault_env("launch")
     plan = adfft.Plan(N, batch=4, dtype=adfft.R32, M=M)
     x = torch.randn((4, N), device="cuda")
-    X = torch.full((4, M), float("nan"), dtype=torch.complex64, device="cuda")
+    X = torch.full((4, M), complex(float("nan"), float("nan")), dtype=torch.complex64, device="cuda")
     with pytest.raises(adfft.AdfftError) as ei:
         plan.execute(x.data_ptr(), X.data_ptr())
     assert ei.value.code == -6              # ADFFT_ERR_CUDA
@@ -90,7 +90,7 @@ def test_skipped_copy_times_out_and_kernel_returns(fault_env):
     plan.set_launch_shape(N // 2, 4, 1, 0)       # staged input: each signal arrives by a bulk copy
     info = plan.info
     assert info.staged == 1
-    X = torch.full((B, M), float("nan"), dtype=torch.complex64, device="cuda")
+    X = torch.full((B, M), complex(float("nan"), float("nan")), dtype=torch.complex64, device="cuda")
     plan.execute(x.data_ptr(), X.data_ptr())
     with pytest.raises(adfft.AdfftError) as ei:
         plan.sync_status()
