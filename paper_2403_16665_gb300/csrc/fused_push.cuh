@@ -53,7 +53,11 @@ struct PushShape {
   static constexpr int NA = KH + 32;         // direct run (k), 32-aligned start
   static constexpr int NB = KH + 64;         // mirrored run (k), at most
   static constexpr int PADA = NA / 32 * 34, PADB = NB / 32 * 34;
-  static constexpr int SLOT = PADA + PADB;   // landing elements per peer
+  // landing elements per peer: the runs, padded so that consecutive slots start 12 elements
+  // apart modulo 16 (96 bytes): the 8-byte loads of one warp step, 4 consecutive elements from
+  // each of 8 sources, then spread over the 32 banks two sources per bank group
+  static constexpr int SLOT0 = PADA + PADB;
+  static constexpr int SLOT = SLOT0 + ((12 - SLOT0 % 16) % 16 + 16) % 16;
   static constexpr int WARPS = T / 32;
   static constexpr int STEPS = JH / 32 / WARPS;   // 32-bin steps per warp per half
   static_assert((1 << LOGP) == P && P >= 2 && P <= 32, "P: a power of two");

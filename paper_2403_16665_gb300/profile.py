@@ -2,6 +2,7 @@
 
     python -m paper_2403_16665_gb300.profile --workload batch_r32 --batch 256 --iters 4
     python -m paper_2403_16665_gb300.profile --workload ragged_r32 --batch 10000 --iters 10
+    python -m paper_2403_16665_gb300.profile --probes [write|dsmem|overlap|l2|place]
 
 Inputs come from the seeded generators in signals.py; every iteration is one
 full adfft_execute of the whole batch.  Prints the mean time per transform
@@ -34,7 +35,12 @@ def main():
     ap.add_argument("--tune", action="store_true", help="autotune the plan first (adfft_plan_autotune)")
     ap.add_argument("--shape", default=None,
                     help="fold launch shape fft_len,cluster,staged[,grid] (adfft_plan_set_launch_shape)")
+    ap.add_argument("--probes", nargs="?", const="all", default=None,
+                    help="build and run the exchange-path micro-benchmarks (write, dsmem, overlap, l2, "
+                         "place or all) instead of a workload")
     args = ap.parse_args()
+    if args.probes:
+        return probes(args.probes)
     _build.build()
     if args.workload == "ragged_r32":
         return ragged(args)
@@ -84,6 +90,19 @@ def main():
           % (args.workload, B, N, M, info.algo, info.fft_len, info.four_step_a, info.residues, info.fold,
              info.cluster, info.staged, info.grid, info.tuned, info.passes,
              args.prec, int(args.adjoint), ms, nbytes / ms / 1e6, B * M / ms * 1e3))
+
+
+def probes(which):
+    """Compile probes/exchange_probes.cu for sm_103a next to the library and run it."""
+    import os
+    import subprocess
+
+    from paper_2403_16665_gb300 import _build
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "probes", "exchange_probes.cu")
+    exe = os.path.join(_build.LIBDIR, "exchange_probes")
+    os.makedirs(_build.LIBDIR, exist_ok=True)
+    subprocess.run([_build.nvcc(), *_build.ARCH, "-O3", "-std=c++17", "-o", exe, src], check=True)
+    return subprocess.run([exe, which]).returncode
 
 
 def _time(fn, iters):
@@ -186,4 +205,5 @@ def ragged(args):
 
 
 if __name__ == "__main__":
-    main()
+    import sys
+    sys.exit(main())
