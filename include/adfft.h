@@ -119,7 +119,14 @@ typedef struct {
                              (ragged plans: every shape class) */
     int32_t grid;         /* clusters the (first) kernel launches; each loops over signals */
     int32_t four_step_a;  /* four-step form: length A of the pass-1 transforms (fft_len = A*B) */
+    int64_t out_bins;     /* output bins written per signal: M, or M/2 + 1 (half spectrum) */
 } adfft_plan_info_t;
+
+/* Output range (adfft_plan_set_output). */
+typedef enum {
+    ADFFT_OUTPUT_FULL = 0,     /* all M bins m = 0 .. M-1 (the default) */
+    ADFFT_OUTPUT_HALF = 1      /* real input: bins m = 0 .. M/2 only ([batch][M/2 + 1] output) */
+} adfft_output_t;
 
 /*
  * Create a plan for `batch` signals of N samples and dense sampling factor
@@ -171,6 +178,19 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo);
 /* Choose the FFT-stage arithmetic (adfft_precision_t); ADFFT_ERR_NOT_SUPPORTED if
  * the plan's dtype or algorithm has no such form. */
 int adfft_plan_set_precision(adfft_plan_t plan, int mode);
+
+/*
+ * Output range.  For a real signal the spectrum is Hermitian, X_{M-m} = conj X_m
+ * (the negative frequencies of Sec. 2, Eq. 2), so bins 0 .. M/2 determine all M.
+ * ADFFT_OUTPUT_HALF makes adfft_execute write only those M/2 + 1 bins
+ * (d_out [batch][M/2 + 1]), half the output bytes; adfft_execute_adjoint then
+ * takes d_grad_out [batch][M/2 + 1] and returns the adjoint of that map (the
+ * real part of S A^H applied to the gradient extended by zeros above M/2).
+ * Served for real plans with even N and M in the single-pass fold form
+ * (ADFFT_ERR_NOT_SUPPORTED otherwise, the plan unchanged); such a plan keeps
+ * to that form (adfft_plan_set_algorithm accepts only ADFFT_ALGO_FOLD and AUTO).
+ */
+int adfft_plan_set_output(adfft_plan_t plan, int mode);
 
 /* Fill *info; ADFFT_ERR_INVALID_ARG for NULL arguments. */
 int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t *info);

@@ -21,6 +21,8 @@ ALGO_AUTO, ALGO_FOLD, ALGO_BLUESTEIN, ALGO_FOUR_STEP = 0, 1, 2, 3
 PREC_NATIVE, PREC_FP16X2, PREC_BF16X3 = 0, 1, 2
 # adfft_plan_autotune flags
 TUNE_WITH_ADJOINT = 1
+# adfft_output_t
+OUTPUT_FULL, OUTPUT_HALF = 0, 1
 
 STATUS = {
     0: "ADFFT_OK", -1: "ADFFT_ERR_INVALID_ARG", -2: "ADFFT_ERR_INVALID_ALPHA",
@@ -37,7 +39,7 @@ EXPORTS = (
     "adfft_plan_get_info", "adfft_plan_workspace_bytes", "adfft_execute",
     "adfft_execute_adjoint", "adfft_execute_host", "adfft_plan_sync_status",
     "adfft_execute_noalloc", "adfft_plan_autotune", "adfft_autotune_save", "adfft_autotune_load",
-    "adfft_autotune_clear", "adfft_plan_set_launch_shape",
+    "adfft_autotune_clear", "adfft_plan_set_launch_shape", "adfft_plan_set_output",
 )
 
 
@@ -52,7 +54,8 @@ class PlanInfo(ctypes.Structure):
                 ("dtype", ctypes.c_int32), ("algo", ctypes.c_int32), ("fft_len", ctypes.c_int64),
                 ("residues", ctypes.c_int64), ("fold", ctypes.c_int64), ("cluster", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("scale", ctypes.c_double), ("staged", ctypes.c_int32),
-                ("tuned", ctypes.c_int32), ("grid", ctypes.c_int32), ("four_step_a", ctypes.c_int32)]
+                ("tuned", ctypes.c_int32), ("grid", ctypes.c_int32), ("four_step_a", ctypes.c_int32),
+                ("out_bins", ctypes.c_int64)]
 
 
 _lib = None
@@ -79,6 +82,7 @@ def load(path: str | None = None):
         "adfft_plan_set_scale": ([vp, f64], i32),
         "adfft_plan_set_algorithm": ([vp, i32], i32),
         "adfft_plan_set_precision": ([vp, i32], i32),
+        "adfft_plan_set_output": ([vp, i32], i32),
         "adfft_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], i32),
         "adfft_plan_workspace_bytes": ([vp], ctypes.c_size_t),
         "adfft_execute": ([vp, vp, vp, vp], i32),
@@ -148,6 +152,12 @@ class Plan:
 
     def set_precision(self, mode):
         _check(self.lib.adfft_plan_set_precision(self._h, int(mode)), "adfft_plan_set_precision")
+        self.info = self.get_info()
+
+    def set_output(self, mode):
+        """OUTPUT_FULL (all M bins) or OUTPUT_HALF (real input: bins 0 .. M/2)."""
+        _check(self.lib.adfft_plan_set_output(self._h, int(mode)), "adfft_plan_set_output")
+        self.info = self.get_info()
 
     def set_launch_shape(self, fft_len=0, cluster=0, staged=-1, grid=0):
         _check(self.lib.adfft_plan_set_launch_shape(self._h, int(fft_len), int(cluster), int(staged), int(grid)),

@@ -133,7 +133,9 @@ struct Plan {
   std::vector<int64_t> in_off, out_off;
 
   size_t in_bytes() const { return (size_t)batch * (size_t)N * in_elem; }
-  size_t out_bytes() const { return (size_t)batch * (size_t)M * out_elem; }
+  bool half = false;                  // real input: output X_0 .. X_{M/2} only (adfft_plan_set_output)
+  int64_t out_bins() const { return half ? M / 2 + 1 : M; }
+  size_t out_bytes() const { return (size_t)batch * (size_t)out_bins() * out_elem; }
 };
 
 // Compile-time-shape kernels of the real classes with a 16384-point packed sub-FFT and one

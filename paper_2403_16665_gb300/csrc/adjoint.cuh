@@ -114,9 +114,15 @@ __global__ void __launch_bounds__(512) adjoint_kernel(const FusedArgs a) {
             const unsigned j = j0 + e * T;
             if (j < jb) {
               g0[e] = g[j];
-              g1[e] = g[j + Mc];
-              g2[e] = g[(M - j) % M];   // g_{M-j} (g_0 for j = 0)
               g3[e] = g[Mc - j];        // g_{Mc-j} (g_Mc for j = 0)
+              if (a.half) {
+                // half-spectrum plans: the bins above M/2 are not part of the map (zero)
+                g1[e] = j == 0 ? g3[e] : czero<V>();
+                g2[e] = j == 0 ? g0[e] : czero<V>();
+              } else {
+                g1[e] = g[j + Mc];
+                g2[e] = g[(M - j) % M];   // g_{M-j} (g_0 for j = 0)
+              }
             }
           }
 #pragma unroll

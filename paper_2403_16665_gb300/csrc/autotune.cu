@@ -110,7 +110,7 @@ std::vector<FoldChoice> fold_candidates(const Plan& p) {
       for (int st : {1, 0})
         for (int grid : {0, -1}) out.push_back(FoldChoice{np, c, st, grid});
       // bulk push exchange (one residue per CTA; configure rejects shapes it has no kernel for)
-      if (c == P && !p.dbl && mode == kLoadRealPacked) out.push_back(FoldChoice{np, c, 2, 0});
+      if (c == P && !p.dbl && mode == kLoadRealPacked && !p.half) out.push_back(FoldChoice{np, c, 2, 0});
     }
   }
   return out;
@@ -170,7 +170,7 @@ int tune_uniform(Plan& p, const void* in, void* out, void* xb, cudaStream_t s, i
     int mode;
     int64_t Nc, Mc;
     core_shape(p, &mode, &Nc, &Mc);
-    const bool pow2 = Nc >= 4 && (Nc & (Nc - 1)) == 0 && mode != kLoadRealPlain;
+    const bool pow2 = Nc >= 4 && (Nc & (Nc - 1)) == 0 && mode != kLoadRealPlain && !p.half;
     for (int64_t A = pow2 ? Nc / 2 : 0; A >= 16 && Nc / A <= 2048; A >>= 1) {
       if (p.tp_ok) release_twopass(p);
       p.tp_force_A = A;

@@ -74,6 +74,9 @@ struct FusedArgs {
   // and waits on input copies give up after wait_limit cycles instead of the default (~2 s)
   long long fault_sig1;
   long long wait_limit;
+  // packed real input only: 1 = write the half spectrum X_0 .. X_{M/2} ([batch][M/2 + 1]
+  // output), which determines the rest by X_{M-m} = conj X_m
+  int half;
 };
 
 // Compile-time shape of a specialised instantiation; a zero field is read from
@@ -147,7 +150,7 @@ __device__ __forceinline__ long long sig_in_bytes(const FusedArgs& a, long long 
   return a.offs ? a.offs[2 * s] : s * a.in_stride * a.in_unit;
 }
 __device__ __forceinline__ long long sig_out_off(const FusedArgs& a, long long s) {
-  return a.offs ? a.offs[2 * s + 1] : s * a.M;
+  return a.offs ? a.offs[2 * s + 1] : s * (a.half ? a.M / 2 + 1 : a.M);
 }
 
 template <typename V>
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
               X2[h] = csub(hA, t);
               if (j <= lim) {
                 st_stream(out + j, X1[h]);
-                st_stream(out + j + Mc, X2[h]);
+                if (!a.half || j == 0) st_stream(out + j + Mc, X2[h]);
               }
             }
             // mirror bins: lanes of residue 0 store their two values in the opposite order, so
@@ -563,7 +566,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
               const unsigned j = (k + (sw ? 1 - h : h)) * P + r_l;
               if (j <= lim && j != 0 && 2 * j != Mc) {
                 st_stream(out + (Mc - j), cconj(y2));
-                st_stream(out + ((unsigned long long)a.M - j), cconj(y1));
+                if (!a.half) st_stream(out + ((unsigned long long)a.M - j), cconj(y1));
               }
             }
           }
@@ -595,10 +598,10 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
               const V X1 = cscale(cadd(E, wO), S);
               const V X2 = cscale(csub(E, wO), S);
               st_stream(out + j, X1);
-              st_stream(out + j + Mc, X2);
+              if (!a.half || j == 0) st_stream(out + j + Mc, X2);
               if (j != 0 && 2 * j != Mc) {
                 st_stream(out + (Mc - j), cconj(X2));
-                st_stream(out + ((unsigned long long)a.M - j), cconj(X1));
+                if (!a.half) st_stream(out + ((unsigned long long)a.M - j), cconj(X1));
               }
             }
           }

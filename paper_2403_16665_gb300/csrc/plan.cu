@@ -286,6 +286,7 @@ int setup_fold(Plan& p, const FoldChoice* forced) {
   core_shape(p, &mode, &Nc, &Mc);
   const int64_t Mt = (mode == kLoadRealPacked) ? p.M : Mc;
   const int64_t sig_bytes = p.stage_ok ? (int64_t)p.N * (int64_t)p.in_elem : 0;
+  if (p.half && (mode != kLoadRealPacked || (forced && forced->stage == 2))) return ADFFT_ERR_UNSUPPORTED_SIZE;
   const int64_t g = gcd64(Mc, Nc);
   int rc = ADFFT_ERR_UNSUPPORTED_SIZE;
   FoldChoice ch{};
@@ -310,6 +311,7 @@ int setup_fold(Plan& p, const FoldChoice* forced) {
   p.fused.args.in_unit = (int)p.in_elem;
   p.fused.args.M = p.M;
   p.fused.args.offs = p.d_offs;
+  p.fused.args.half = p.half ? 1 : 0;
   if (p.fault.copy_skip >= 0) {
     p.fused.args.fault_sig1 = p.fault.copy_skip + 1;
     p.fused.args.wait_limit = 20000000;   // ~10 ms of SM clock
@@ -862,8 +864,10 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
     p.algo = p.auto_algo;
     return ADFFT_OK;
   }
+  if (p.half && algo != ADFFT_ALGO_FOLD) return ADFFT_ERR_NOT_SUPPORTED;   // half spectrum: single pass only
   if (algo == ADFFT_ALGO_FOLD) {
     // the single-pass fold form, else (sub-FFT beyond one cluster) its two-pass variant
+    if (p.half && !p.fold_ok) return ADFFT_ERR_NOT_SUPPORTED;
     if (!p.fold_ok && !p.tp_ok) return ADFFT_ERR_NOT_SUPPORTED;
     p.algo = p.fold_ok ? ADFFT_ALGO_FOLD : ADFFT_ALGO_FOUR_STEP;
     return ADFFT_OK;
@@ -880,6 +884,34 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
   if (rc == ADFFT_ERR_UNSUPPORTED_SIZE) return ADFFT_ERR_NOT_SUPPORTED;
   if (rc != ADFFT_OK) return rc;
   p.algo = algo;
+  return ADFFT_OK;
+}
+
+int adfft_plan_set_output(adfft_plan_t plan, int mode) {
+  using namespace adfft;
+  if (!plan || (mode != ADFFT_OUTPUT_FULL && mode != ADFFT_OUTPUT_HALF)) return ADFFT_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  const bool want = mode == ADFFT_OUTPUT_HALF;
+  if (want == p.half) return ADFFT_OK;
+  if (want) {
+    // real input packed two samples per element (even N and M), single-pass fold form
+    int m;
+    int64_t Nc, Mc;
+    core_shape(p, &m, &Nc, &Mc);
+    if (p.ragged || m != kLoadRealPacked || !p.fold_ok) return ADFFT_ERR_NOT_SUPPORTED;
+  }
+  const bool old = p.half;
+  const FoldChoice keep = p.fold_choice;
+  p.half = want;
+  FoldChoice c = keep;
+  if (want && c.stage == 2) c.stage = -1;   // the push form writes the full spectrum only
+  int rc = p.fold_ok ? setup_fold(p, &c) : ADFFT_OK;
+  if (rc != ADFFT_OK) {
+    p.half = old;
+    setup_fold(p, &keep);
+    return rc == ADFFT_ERR_UNSUPPORTED_SIZE ? ADFFT_ERR_NOT_SUPPORTED : rc;
+  }
+  if (p.fold_ok) p.algo = ADFFT_ALGO_FOLD;
   return ADFFT_OK;
 }
 
@@ -925,6 +957,7 @@ int adfft_plan_get_info(adfft_plan_t plan, adfft_plan_info_t* info) {
   info->batch = p.batch;
   info->dtype = p.dtype;
   info->algo = p.algo;
+  info->out_bins = p.ragged ? 0 : p.out_bins();
   if (p.ragged) {
     info->batch = p.r_count;
     info->fft_len = 0;

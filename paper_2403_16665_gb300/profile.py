@@ -35,6 +35,7 @@ def main():
     ap.add_argument("--tune", action="store_true", help="autotune the plan first (adfft_plan_autotune)")
     ap.add_argument("--shape", default=None,
                     help="fold launch shape fft_len,cluster,staged[,grid] (adfft_plan_set_launch_shape)")
+    ap.add_argument("--half", action="store_true", help="half-spectrum output (real input: bins 0 .. M/2)")
     ap.add_argument("--probes", nargs="?", const="all", default=None,
                     help="build and run the exchange-path micro-benchmarks (write, dsmem, overlap, l2, "
                          "place or all) instead of a workload")
@@ -63,7 +64,9 @@ def main():
         plan.set_algorithm(args.algo)
     if args.prec != adfft.PREC_NATIVE:
         plan.set_precision(args.prec)
-    X = torch.empty((B, M), dtype=adfft.out_dtype(x.dtype), device=dev)
+    if args.half:
+        plan.set_output(adfft.OUTPUT_HALF)
+    X = torch.empty((B, plan.info.out_bins), dtype=adfft.out_dtype(x.dtype), device=dev)
     if args.shape:
         plan.set_launch_shape(*(int(v) for v in args.shape.split(",")))
     if args.tune:
@@ -83,7 +86,7 @@ def main():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(1, args.iters)
     info = plan.info
-    nbytes = x.numel() * x.element_size() + B * M * X.element_size()
+    nbytes = x.numel() * x.element_size() + X.numel() * X.element_size()
     print("workload=%s B=%d N=%d M=%d algo=%d fft_len=%d A=%d P=%d q=%d C=%d staged=%d grid=%d tuned=%d passes=%d "
           "prec=%d adjoint=%d  "
           "%.4f ms/transform  %.1f GB/s (input + output bytes)  %.3e points/s"
