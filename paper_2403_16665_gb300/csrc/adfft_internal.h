@@ -51,6 +51,16 @@ struct BluesteinLaunch {
   size_t smem;
 };
 
+// Launch geometry of the chirp-z adjoint kernel.
+struct BluesteinAdjLaunch {
+  BluesteinAdjArgs args;
+  int r0;
+  bool dbl;
+  int threads;
+  int grid_y;
+  size_t smem;
+};
+
 // Launch geometry of the second pass of the two-pass form.
 struct TwoPassLaunch {
   TwoPassArgs args;
@@ -99,6 +109,12 @@ struct Plan {
   void* d_blu_tw = nullptr;           // W_L table
   void* d_chirp = nullptr;            // chirp c_j
   void* d_H = nullptr;                // per-chunk kernel spectra
+  // chirp-z adjoint (set up at the first adjoint call of a plan without a fold form)
+  bool bla_ok = false;
+  BluesteinAdjLaunch bla{};
+  void* d_bla_tw = nullptr;           // W_L table of the adjoint's transform length
+  void* d_bla_chirp = nullptr;        // chirp c_j, j < max(N, M)
+  void* d_bla_H = nullptr;            // kernel spectra per block difference
 
   // two-pass path (sub-FFT beyond one cluster): pass 1 = fused kColumns launch, pass 2 = columns
   bool tp_ok = false;
@@ -167,6 +183,7 @@ void core_shape(const Plan& p, int* mode, int64_t* Nc, int64_t* Mc);
 int setup_fold(Plan& p, const FoldChoice* forced = nullptr);
 int setup_twopass(Plan& p);
 int setup_bluestein(Plan& p);
+int setup_bluestein_adjoint(Plan& p);
 void release_twopass(Plan& p);
 int prepare_precision(Plan& p);   // function attributes of the precision-form kernels in use
 int64_t plan_gcd(int64_t a, int64_t b);
@@ -204,6 +221,9 @@ cudaError_t tc_launch_columns_bf16(const TwoPassLaunch& L, const void* scratch, 
 // Chirp-z launchers (bluestein.cu).
 cudaError_t bluestein_prepare(const BluesteinLaunch& L);
 cudaError_t bluestein_launch(const BluesteinLaunch& L, const void* in, void* out, cudaStream_t stream);
+cudaError_t bluestein_adjoint_prepare(const BluesteinAdjLaunch& L);
+cudaError_t bluestein_adjoint_launch(const BluesteinAdjLaunch& L, const void* g, void* xb, cudaStream_t stream);
+constexpr int kBlaAccF32 = 16, kBlaAccF64 = 8;   // output samples per thread of the chirp-z adjoint
 
 }  // namespace adfft
 

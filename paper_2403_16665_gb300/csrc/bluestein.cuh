@@ -97,4 +97,90 @@ __global__ void __launch_bounds__(512) bluestein_kernel(const BluesteinArgs b) {
   }
 }
 
+// Adjoint of the chirp-z evaluation (the backward pass of a chirp-z plan):
+//     xb_n = S sum_{m<M} conj(W_M^{mn}) g_m = S conj(c_n) sum_m (g_m conj(c_m)) c_{n-m},
+// (conj W_M^{mn} = conj(c_m) conj(c_n) c_{m-n}, and c is even), i.e. the convolution of
+// b_m = g_m conj(c_m) (length M) with the chirp itself, read at n < N.  The input is cut
+// into blocks of Bi bins [m0, m0 + Bi) and the output into chunks of Bo samples
+// [n0, n0 + Bo); with the chirp segment v_i = c_{n0 - m0 - (Bi-1) + i}, i < Bi + Bo - 1,
+// a block contributes (u * v)[t + Bi - 1] to output n0 + t (u the block of b), which is
+// the length-L circular convolution for L >= Bi + Bo - 1.  FFT_L(v)/L depends on
+// n0 - m0 only and is precomputed per difference on the host in double precision.
+// One CTA per (signal, output chunk) runs every input block in turn and accumulates its
+// chunk in registers; then xb_{n0+t} = S conj(c_{n0+t}) acc_t (its real part for real
+// input).
+struct BluesteinAdjArgs {
+  FusedArgs f;          // FFT view: Np = L, RPC = 1, Mt = L, tw = W_L table, region, nrad
+  const void* chirp;    // c_j, j < max(N, M)
+  const void* H;        // (nI + nO - 1) x L kernel spectra (divided by L), index o - i + nI - 1
+  long long N;          // output samples per signal
+  int Bi, Bo, nI, nO;   // input block, output chunk, their counts
+  int real_out;         // real input plan: write the real part
+};
+
+template <typename V, int VPT, int R0, int ACC>
+__global__ void __launch_bounds__(512) bluestein_adjoint_kernel(const BluesteinAdjArgs b) {
+  using Rl = typename real_of<V>::type;
+  const FusedArgs& a = b.f;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tw_n = a.tw_lo_n + a.tw_hi_n;
+  const FusedSmem L = fused_smem_layout(tw_n, 0, 1, a.region, (int)sizeof(V));
+  V* tw_s = reinterpret_cast<V*>(smem_raw + L.tw);
+  V* buf = reinterpret_cast<V*>(smem_raw + L.buf);
+  for (int i = threadIdx.x; i < tw_n; i += blockDim.x) tw_s[i] = reinterpret_cast<const V*>(a.tw)[i];
+  __syncthreads();
+  TwTable<V> tab{tw_s, tw_s + a.tw_lo_n, a.tw_bits, (1u << a.tw_bits) - 1u};
+
+  const unsigned Lf = (unsigned)a.Np;
+  const unsigned T = blockDim.x;
+  const int o = (int)blockIdx.x;
+  const long long n0 = (long long)o * b.Bo;
+  const int nb = (int)min((long long)b.Bo, b.N - n0);
+  const long long M = a.M;
+  const V* chirp = reinterpret_cast<const V*>(b.chirp);
+  const Rl S = (Rl)a.scale;
+
+  for (long long sig = blockIdx.y; sig < a.batch; sig += gridDim.y) {
+    const V* g = reinterpret_cast<const V*>(a.in) + sig_out_off(a, sig);
+    V acc[ACC];
+#pragma unroll
+    for (int e = 0; e < ACC; ++e) acc[e] = czero<V>();
+    for (int i = 0; i < b.nI; ++i) {
+      const long long m0 = (long long)i * b.Bi;
+      const long long mb = min((long long)b.Bi, M - m0);
+      // u_s = g_{m0+s} conj(c_{m0+s}), zero padded to L
+      for (unsigned idx = threadIdx.x; idx < Lf; idx += T) {
+        V v = czero<V>();
+        if ((long long)idx < mb) v = cmulc(__ldg(g + m0 + idx), __ldg(chirp + m0 + idx));
+        buf[pad16((int)idx)] = v;
+      }
+      __syncthreads();
+      run_all_passes<V, VPT, R0>(a, buf, tab);
+      const V* H = reinterpret_cast<const V*>(b.H) + (size_t)(o - i + b.nI - 1) * Lf;
+      for (unsigned idx = threadIdx.x; idx < Lf; idx += T) {
+        const int p = pad16((int)idx);
+        buf[p] = cconj(cmul(buf[p], __ldg(H + idx)));
+      }
+      __syncthreads();
+      run_all_passes<V, VPT, R0>(a, buf, tab);
+#pragma unroll
+      for (int e = 0; e < ACC; ++e) {
+        const int t = (int)threadIdx.x + e * (int)T;
+        if (t < nb) acc[e] = cadd(acc[e], cconj(buf[pad16(t + b.Bi - 1)]));
+      }
+      __syncthreads();
+    }
+    const long long ob = a.offs ? a.offs[2 * sig] / a.in_unit : sig * b.N;
+#pragma unroll
+    for (int e = 0; e < ACC; ++e) {
+      const int t = (int)threadIdx.x + e * (int)T;
+      if (t < nb) {
+        const V y = cscale(cmulc(acc[e], __ldg(chirp + n0 + t)), S);   // S conj(c_n) acc
+        if (b.real_out) reinterpret_cast<Rl*>(a.out)[ob + n0 + t] = y.x;
+        else reinterpret_cast<V*>(a.out)[ob + n0 + t] = y;
+      }
+    }
+  }
+}
+
 }  // namespace adfft

@@ -532,6 +532,103 @@ std::vector<T> flatten(const std::vector<std::complex<double>>& v) {
 
 }  // namespace
 
+// Configure the chirp-z adjoint (any N, M): input blocks and output chunks of one transform
+// length L (a single tile where N + M - 1 fits), FP64-derived chirp and kernel spectra.
+int setup_bluestein_adjoint(Plan& p) {
+  if (p.bla_ok) return ADFFT_OK;
+  const int64_t Lmax = p.dbl ? 8192 : 16384;
+  const int acc = p.dbl ? kBlaAccF64 : kBlaAccF32;
+  const int vpt = fused_values_per_thread(p.dbl);
+  const size_t esz = p.dbl ? 16 : 8;
+  int64_t L = 1, Bi, Bo;
+  if (p.N + p.M - 1 <= Lmax && p.N <= (int64_t)acc * kMaxThreads) {
+    while (L < p.N + p.M - 1) L <<= 1;
+    Bi = p.M;
+    Bo = p.N;
+  } else {
+    L = Lmax;
+    Bi = Bo = L / 2;
+  }
+  const int64_t nI = (p.M + Bi - 1) / Bi, nO = (p.N + Bo - 1) / Bo;
+  if (nO > 65535 || p.M >= (int64_t(1) << 31)) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  int threads = (int)std::max<int64_t>(L / vpt, (Bo + acc - 1) / acc);
+  threads = std::max(32, (threads + 31) / 32 * 32);
+  if (threads > kMaxThreads) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  const int bits = (ilog2(L) + 1) / 2;
+  const int tw_n = (1 << bits) + (int)((L + (1 << bits) - 1) >> bits);
+  const int64_t region = L + L / 16 + 2;
+  const FusedSmem lay = fused_smem_layout(tw_n, 0, 1, (int)region, (int)esz);
+  if ((size_t)lay.total > kSmemLimit) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  // host tables: chirp, kernel spectra of every block difference d = (o - i) Bo (single tile: 0)
+  std::vector<std::complex<double>> ch((size_t)std::max(p.N, p.M));
+  for (size_t j = 0; j < ch.size(); ++j) ch[j] = chirp((int64_t)j, p.M);
+  const int64_t nd = nI + nO - 1;
+  std::vector<std::complex<double>> H((size_t)(nd * L));
+  std::vector<std::complex<double>> seg((size_t)L);
+  for (int64_t k = 0; k < nd; ++k) {
+    const int64_t d = (k - (nI - 1)) * Bo;
+    std::fill(seg.begin(), seg.end(), std::complex<double>(0, 0));
+    for (int64_t i = 0; i < Bi + Bo - 1 && i < L; ++i) seg[(size_t)i] = chirp(d - (Bi - 1) + i, p.M);
+    host_fft(seg);
+    for (int64_t t = 0; t < L; ++t) H[(size_t)(k * L + t)] = seg[(size_t)t] / (double)L;
+  }
+  int lo_n, hi_n, rc;
+  if (p.dbl) {
+    if ((rc = upload(&p.d_bla_tw, build_two_level<double>(L, bits, &lo_n, &hi_n))) != ADFFT_OK) return rc;
+    if ((rc = upload(&p.d_bla_chirp, flatten<double>(ch))) != ADFFT_OK) return rc;
+    if ((rc = upload(&p.d_bla_H, flatten<double>(H))) != ADFFT_OK) return rc;
+  } else {
+    if ((rc = upload(&p.d_bla_tw, build_two_level<float>(L, bits, &lo_n, &hi_n))) != ADFFT_OK) return rc;
+    if ((rc = upload(&p.d_bla_chirp, flatten<float>(ch))) != ADFFT_OK) return rc;
+    if ((rc = upload(&p.d_bla_H, flatten<float>(H))) != ADFFT_OK) return rc;
+  }
+  BluesteinAdjLaunch& BL = p.bla;
+  BluesteinAdjArgs& b = BL.args;
+  memset(&b, 0, sizeof(b));
+  FusedArgs& a = b.f;
+  a.batch = p.batch;
+  a.M = p.M;
+  a.Np = (int)L;
+  a.logNp = ilog2(L);
+  a.P = 1;
+  a.q = 1;
+  a.RPC = 1;
+  a.C = 1;
+  a.Nc = (int)L;
+  a.Mc = (int)L;
+  a.Mt = (int)L;
+  a.tw_bits = bits;
+  a.tw_lo_n = lo_n;
+  a.tw_hi_n = hi_n;
+  a.tw = p.d_bla_tw;
+  a.scale = p.scale;
+  a.region = (int)region;
+  const int lr0 = (a.logNp == 0) ? 0 : (a.logNp % 4 ? a.logNp % 4 : 4);
+  a.nrad = 1 + (a.logNp - lr0) / 4;
+  a.in_unit = (int)p.in_elem;
+  a.offs = p.d_offs;
+  b.chirp = p.d_bla_chirp;
+  b.H = p.d_bla_H;
+  b.N = p.N;
+  b.Bi = (int)Bi;
+  b.Bo = (int)Bo;
+  b.nI = (int)nI;
+  b.nO = (int)nO;
+  b.real_out = p.real ? 1 : 0;
+  BL.r0 = 1 << lr0;
+  BL.dbl = p.dbl;
+  BL.threads = threads;
+  BL.grid_y = (int)std::max<int64_t>(1, std::min<int64_t>(p.batch, 65535));
+  BL.smem = (size_t)lay.total;
+  cudaError_t e = bluestein_adjoint_prepare(BL);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  p.bla_ok = true;
+  return ADFFT_OK;
+}
+
 // Configure the chirp-z path (any N, M); returns ADFFT_OK or why it does not apply.
 int setup_bluestein(Plan& p) {
   if (p.blu_ok) return ADFFT_OK;
@@ -659,7 +756,12 @@ int launch_adjoint(Plan& p, const void* g, void* xb, cudaStream_t s) {
   cudaError_t e;
   // the selected fold form, else whichever fold form the plan has (the chirp-z form has no adjoint kernel)
   const bool use_tp = p.tp_ok && (p.algo == ADFFT_ALGO_FOUR_STEP || !p.fold_ok);
-  if (!use_tp && p.fold_ok) {
+  if (p.algo == ADFFT_ALGO_BLUESTEIN || (!p.fold_ok && !p.tp_ok)) {
+    // chirp-z plans: the adjoint's own tables are set up at its first call
+    const int rc = setup_bluestein_adjoint(p);
+    if (rc != ADFFT_OK) return rc == ADFFT_ERR_UNSUPPORTED_SIZE ? ADFFT_ERR_NOT_SUPPORTED : rc;
+    e = bluestein_adjoint_launch(p.bla, g, xb, s);
+  } else if (!use_tp && p.fold_ok) {
     e = adjoint_launch(p.fused, g, xb, s);
   } else if (use_tp) {
     // transpose of the two passes, in reverse order, through the same workspace
@@ -692,7 +794,8 @@ namespace {
 
 void release(Plan& p) {
   if (p.ragged) ragged_release(p);
-  for (void** q : {&p.d_blu_tw, &p.d_chirp, &p.d_H, &p.d_tp_tw1, &p.d_tp_post, &p.d_tp_tw2, &p.d_tp_wM, &p.d_ws}) {
+  for (void** q : {&p.d_blu_tw, &p.d_chirp, &p.d_H, &p.d_bla_tw, &p.d_bla_chirp, &p.d_bla_H, &p.d_tp_tw1,
+                   &p.d_tp_post, &p.d_tp_tw2, &p.d_tp_wM, &p.d_ws}) {
     if (*q) cudaFree(*q);
     *q = nullptr;
   }

@@ -94,11 +94,52 @@ def test_single_real_fp64_chirp_z():
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-12
 
 
-def test_adjoint_unavailable_without_fold():
+@pytest.mark.parametrize("code,N,M,batch,force", [
+    (adfft.C64, 1000, 2500, 2, False),       # chirp-z only (no power-of-two common divisor): one tile
+    (adfft.R32, 1000, 2500, 3, False),
+    (adfft.C128, 300, 700, 2, False),
+    (adfft.R64, 1000, 2500, 2, False),
+    (adfft.C64, 8192, 20480, 2, True),       # forced chirp-z: N + M - 1 > L, input in 3 blocks
+    (adfft.C64, 1024, 100000, 1, True),      # 13 input blocks
+    (adfft.R32, 6000, 15000, 2, False),      # 2 output chunks x 2 input blocks
+    (adfft.C128, 3000, 7500, 1, False),      # fp64: L = 8192, blocks of 4096
+])
+def test_chirp_z_adjoint_matches_oracle(code, N, M, batch, force):
+    """The chirp-z adjoint (correlation of g conj(c) with the chirp, blocked) against the
+    oracle's explicit adjoint of Eq. 7 at every output sample."""
     torch = _torch()
-    plan = adfft.Plan(1000, batch=1, dtype=adfft.C64, M=2500)
-    g = torch.zeros((1, 2500), dtype=torch.complex64, device="cuda")
-    xb = torch.zeros((1, 1000), dtype=torch.complex64, device="cuda")
-    with pytest.raises(adfft.AdfftError) as e:
-        plan.execute_adjoint(g.data_ptr(), xb.data_ptr())
-    assert e.value.code == -9
+    real = code in (adfft.R32, adfft.R64)
+    dbl = code in (adfft.R64, adfft.C128)
+    rng = np.random.default_rng(N + M)
+    g = (rng.standard_normal((batch, M)) + 1j * rng.standard_normal((batch, M))).astype(
+        np.complex128 if dbl else np.complex64)
+    plan = adfft.Plan(N, batch=batch, dtype=code, M=M)
+    if force:
+        plan.set_algorithm(adfft.ALGO_BLUESTEIN)
+    assert plan.info.algo == adfft.ALGO_BLUESTEIN
+    gt = torch.from_numpy(g).cuda()
+    xt = torch.float64 if (real and dbl) else torch.float32 if real else torch.complex128 if dbl else torch.complex64
+    xb = torch.empty((batch, N), dtype=xt, device="cuda")
+    plan.execute_adjoint(gt.data_ptr(), xb.data_ptr())
+    plan.sync_status()
+    ref = oracle.alpha_dft_adjoint(g.astype(np.complex128), N, real_input=real)
+    got = xb.cpu().numpy()
+    err = (np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)).max()
+    assert err <= (1e-12 if dbl else 2e-6 * np.log2(M)), err
+
+
+def test_chirp_z_adjoint_dot_product():
+    """<A x, g> = <x, A^H g> through the chirp-z forward and adjoint launches."""
+    torch = _torch()
+    N, M = 1000, 2500
+    x = torch.randn((2, N), dtype=torch.complex128, device="cuda")
+    g = torch.randn((2, M), dtype=torch.complex128, device="cuda")
+    plan = adfft.Plan(N, batch=2, dtype=adfft.C128, M=M)
+    X = torch.empty((2, M), dtype=torch.complex128, device="cuda")
+    xb = torch.empty_like(x)
+    plan.execute(x.data_ptr(), X.data_ptr())
+    plan.execute_adjoint(g.data_ptr(), xb.data_ptr())
+    plan.sync_status()
+    lhs = torch.vdot(g.flatten(), X.flatten())
+    rhs = torch.vdot(xb.flatten(), x.flatten())
+    assert abs((lhs - rhs).item()) <= 1e-11 * abs(lhs.item())
