@@ -119,3 +119,73 @@ def test_ragged_loss_gradient():
         got = gx[in_off[i]:in_off[i + 1]].cpu().numpy()
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-6 * np.log2(M)
     lib.adfft_plan_destroy(h)
+
+
+def _c5_plan(torch):
+    x_np, Ns, alphas, _ = signals.ragged_r32(count=10000)
+    plan = adfft.RaggedPlan(Ns, alphas, adfft.R32)
+    return x_np, np.asarray(Ns), np.asarray(alphas), plan
+
+
+def test_ragged_c5_adjoint_every_class_against_oracle():
+    """The 10000-signal ragged workload: the adjoint of one signal of every shape class
+    (including the 16384-point classes with clusters of up to 16 CTAs and N = 65536) against
+    the oracle's explicit adjoint on sampled output samples."""
+    torch = _torch()
+    x_np, Ns, alphas, plan = _c5_plan(torch)
+    Ms = np.rint(alphas * Ns).astype(np.int64)
+    rng = np.random.default_rng(21)
+    dev = torch.device("cuda:0")
+    g = torch.randn(int(plan.out_off[-1]), dtype=torch.complex64, device=dev)
+    xb = torch.empty(int(plan.in_off[-1]), dtype=torch.float32, device=dev)
+    plan.execute_adjoint(g.data_ptr(), xb.data_ptr())
+    plan.sync_status()
+    first = {}
+    for i, key in enumerate(zip(Ns.tolist(), Ms.tolist())):
+        first.setdefault(key, i)
+    assert len(first) >= 40
+    for (N, M), i in sorted(first.items()):
+        gi = g[plan.out_off[i]:plan.out_off[i + 1]].cpu().numpy().astype(np.complex128)
+        samples = np.unique(np.concatenate([[0, 1, N - 1, N // 2], rng.integers(0, N, 12)]))
+        ref = oracle.alpha_dft_adjoint(gi, N, real_input=True, samples=samples)
+        got = xb[plan.in_off[i]:plan.in_off[i + 1]][torch.from_numpy(samples).to(dev)].cpu().numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 2e-6 * np.log2(M), (N, M, err)
+
+
+def test_ragged_c5_fp32_gradient_directional_difference():
+    """FP32 gradient of L = sum |X_m - Y_m|^2 over the whole 10000-signal ragged workload
+    (Y complex Gaussian): the central difference (L(x + e d) - L(x - e d)) / (2 e) along
+    random +-1 directions, which is exact for a quadratic L up to rounding, against
+    <grad, d> with grad = Re(A^H 2 (X - Y)) from the ragged adjoint.  One direction over
+    every sample, and one confined to the signals of the N = 65536 classes."""
+    torch = _torch()
+    x_np, Ns, alphas, plan = _c5_plan(torch)
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(x_np).to(dev)
+    nb = int(plan.out_off[-1])
+    gen = torch.Generator(device=dev).manual_seed(5)
+    Y = torch.randn(nb, dtype=torch.complex64, device=dev, generator=gen)
+    X = torch.empty(nb, dtype=torch.complex64, device=dev)
+
+    def loss(xv):
+        plan.execute(xv.data_ptr(), X.data_ptr())
+        plan.sync_status()
+        return (X - Y).abs().double().pow(2).sum().item()
+
+    loss(x)
+    gout = 2 * (X - Y)
+    grad = torch.empty_like(x)
+    plan.execute_adjoint(gout.data_ptr(), grad.data_ptr())
+    plan.sync_status()
+    big = torch.zeros_like(x)
+    for i in np.flatnonzero(Ns == 65536):
+        big[plan.in_off[i]:plan.in_off[i + 1]] = 1.0
+    for mask in (None, big):
+        d = torch.randint(0, 2, x.shape, device=dev, generator=gen).float() * 2 - 1
+        if mask is not None:
+            d = d * mask
+        eps = 0.5
+        fd = (loss(x + eps * d) - loss(x - eps * d)) / (2 * eps)
+        an = (grad.double() * d.double()).sum().item()
+        assert abs(fd - an) <= 1e-4 * abs(an), (fd, an)
