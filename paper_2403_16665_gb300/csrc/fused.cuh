@@ -386,7 +386,11 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   V* tw_s = reinterpret_cast<V*>(smem_raw + L.tw);
   unsigned char* stage = smem_raw + L.stage;
   V* buf = reinterpret_cast<V*>(smem_raw + L.buf);
-  const bool staged = a.stage_bytes > 0;
+  // staged: each signal's contiguous input arrives by a bulk copy (prefetched one signal
+  // ahead); col_staged (columns of the two-pass form): the CTA gathers its strided column into
+  // shared memory once, so the first pass reads it from there for every residue
+  const bool staged = a.stage_bytes > 0 && MODE != kColumns;
+  const bool col_staged = a.stage_bytes > 0 && MODE == kColumns;
 
   if (threadIdx.x == 0 && staged) {
     mbar_init(bar, 1);
@@ -458,6 +462,21 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     } else if (MODE == kColumns) {
       u = reinterpret_cast<const V*>(reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, sig / a.cols)) +
           (sig % a.cols);
+      if (col_staged) {
+        // 4 strided loads in flight per thread; the previous first pass is done with `stage`
+        V* st = reinterpret_cast<V*>(stage);
+        const unsigned ncol = (unsigned)a.Nc, T = blockDim.x;
+        for (unsigned i0 = threadIdx.x; i0 < ncol; i0 += 4 * T) {
+          V v[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (i0 + e * T < ncol) v[e] = ld_col<V>(u, (int)(i0 + e * T), a.cols);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (i0 + e * T < ncol) st[i0 + e * T] = v[e];
+        }
+        __syncthreads();
+      }
     } else {
       u = reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, sig);
     }
@@ -467,7 +486,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     // ---- K1: fold + residue twiddle + first radix
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
     if (!failed) {
-      if (staged) first_pass<R0, V, true, SH>(a, u, reinterpret_cast<const V*>(stage), MODE, buf, tab, r0);
+      if (staged || col_staged) first_pass<R0, V, true, SH>(a, u, reinterpret_cast<const V*>(stage), MODE, buf, tab, r0);
       else first_pass<R0, V, false, SH>(a, u, nullptr, MODE, buf, tab, r0);
     }
     __syncthreads();

@@ -357,7 +357,9 @@ int setup_twopass(Plan& p) {
       // pass 1: alpha-DFT of the B columns (A samples -> R1 bins each)
       FusedLaunch L1{};
       void* tw1 = nullptr;
-      int rc = configure_fused(p.dbl, kColumns, A, R1, R1, p.batch * B, 0, max_c, 1.0, p.d_status, L1, &tw1);
+      // the column (A complex elements) is gathered into shared memory once per CTA where it fits
+      int rc = configure_fused(p.dbl, kColumns, A, R1, R1, p.batch * B, A * (int64_t)esz, max_c, 1.0, p.d_status,
+                               L1, &tw1);
       if (rc != ADFFT_OK) {
         if (tw1) cudaFree(tw1);
         if (rc == ADFFT_ERR_UNSUPPORTED_SIZE) continue;
