@@ -155,6 +155,31 @@ adfft_plan_t adfft_plan_create_bins(int64_t N, int64_t M, int64_t batch, int dty
 adfft_plan_t adfft_plan_create_ragged(const int64_t *N, const double *alpha, int64_t count,
                                       int dtype);
 
+/* Forward form of a ragged plan (adfft_plan_set_ragged_form). */
+typedef enum {
+    ADFFT_RAGGED_CLASSES = 0,  /* one persistent launch per shape class, all captured in one
+                                  CUDA graph (forked over internal streams); the default */
+    ADFFT_RAGGED_QUEUE = 1     /* one persistent kernel for the whole batch over a work queue
+                                  of tiles (an option: slower on the 10000-signal mix) */
+} adfft_ragged_form_t;
+
+/*
+ * Choose how a ragged plan's forward transform runs.  ADFFT_RAGGED_QUEUE: one persistent
+ * kernel (as many CTAs as are resident) takes tiles from a queue in order: a "whole" tile
+ * transforms signals whose residue FFTs fit one CTA's shared memory (several signals of a
+ * class in turn); a longer signal is split into "fft" tiles (a group of its residues, the
+ * sub-FFT results written to plan workspace) followed in the queue by "unpack" tiles (a
+ * range of its output bins, gathered from that workspace once its fft tiles are counted;
+ * the wait is bounded).  The execute is a memset of the queue counters plus that launch,
+ * captured in a CUDA graph like the other form.  Served when every shape class is FP32 or
+ * complex64 with even N and M for real input (packed) and a fold of at most 64 blocks onto
+ * a power-of-two sub-FFT of at most 16384 points dividing its length and bin count; plan
+ * workspace = 8 bytes per packed bin of the split signals (those whose residue FFTs exceed
+ * 16384 points).  ADFFT_ERR_NOT_SUPPORTED for
+ * plans it cannot serve or non-ragged plans.  The adjoint always uses the class graph.
+ */
+int adfft_plan_set_ragged_form(adfft_plan_t plan, int form);
+
 /* Packed offsets of a ragged plan (arrays of count+1 entries; either may be NULL).
  * For a uniform plan: in_off[i] = i*N, out_off[i] = i*M. */
 int adfft_plan_offsets(adfft_plan_t plan, int64_t *in_off, int64_t *out_off);

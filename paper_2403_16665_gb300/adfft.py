@@ -23,6 +23,8 @@ PREC_NATIVE, PREC_FP16X2, PREC_BF16X3 = 0, 1, 2
 TUNE_WITH_ADJOINT = 1
 # adfft_output_t
 OUTPUT_FULL, OUTPUT_HALF = 0, 1
+# adfft_ragged_form_t
+RAGGED_CLASSES, RAGGED_QUEUE = 0, 1
 
 STATUS = {
     0: "ADFFT_OK", -1: "ADFFT_ERR_INVALID_ARG", -2: "ADFFT_ERR_INVALID_ALPHA",
@@ -40,6 +42,7 @@ EXPORTS = (
     "adfft_execute_adjoint", "adfft_execute_host", "adfft_plan_sync_status",
     "adfft_execute_noalloc", "adfft_plan_autotune", "adfft_autotune_save", "adfft_autotune_load",
     "adfft_autotune_clear", "adfft_plan_set_launch_shape", "adfft_plan_set_output",
+    "adfft_plan_set_ragged_form",
 )
 
 
@@ -83,6 +86,7 @@ def load(path: str | None = None):
         "adfft_plan_set_algorithm": ([vp, i32], i32),
         "adfft_plan_set_precision": ([vp, i32], i32),
         "adfft_plan_set_output": ([vp, i32], i32),
+        "adfft_plan_set_ragged_form": ([vp, i32], i32),
         "adfft_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], i32),
         "adfft_plan_workspace_bytes": ([vp], ctypes.c_size_t),
         "adfft_execute": ([vp, vp, vp, vp], i32),
@@ -230,9 +234,19 @@ class RaggedPlan(Plan):
         self.lib = lib
         self.info = self.get_info()
         self.in_off = np.zeros(Na.size + 1, dtype=np.int64)
+        self.form = None
         self.out_off = np.zeros(Na.size + 1, dtype=np.int64)
         _check(lib.adfft_plan_offsets(self._h, self.in_off.ctypes.data_as(ctypes.c_void_p),
                                       self.out_off.ctypes.data_as(ctypes.c_void_p)), "adfft_plan_offsets")
+
+
+def _ragged_set_form(self, form):
+    """RAGGED_CLASSES (graph of per-class launches) or RAGGED_QUEUE (one persistent kernel)."""
+    _check(self.lib.adfft_plan_set_ragged_form(self._h, int(form)), "adfft_plan_set_ragged_form")
+    self.form = int(form)
+
+
+RaggedPlan.set_form = _ragged_set_form
 
 
 def autotune_save(path):

@@ -11,6 +11,7 @@
 #include "fused.cuh"
 #include "bluestein.cuh"
 #include "twopass.cuh"
+#include "ragged_queue.cuh"
 
 struct adfft_plan_s;
 
@@ -138,6 +139,13 @@ struct Plan {
   cudaStream_t r_streams[kRaggedStreams] = {};
   cudaEvent_t r_fork = nullptr, r_join[kRaggedStreams] = {};
   cudaGraphExec_t r_graph[2] = {nullptr, nullptr};   // forward, adjoint
+  // ragged forward as one persistent kernel over a tile queue (ragged_queue.cuh)
+  bool rq_ok = false;                 // the queue form serves this plan
+  bool rq_on = false;                 // the forward uses it (adfft_plan_set_ragged_form)
+  RqArgs rq{};                        // kernel arguments (buffers of the plan)
+  int rq_grid = 0;
+  size_t rq_smem = 0;
+  std::vector<void*> rq_bufs;         // device allocations of the queue form
   const void* r_graph_in[2] = {nullptr, nullptr};
   void* r_graph_out[2] = {nullptr, nullptr};
 
@@ -187,6 +195,8 @@ int setup_bluestein_adjoint(Plan& p);
 void release_twopass(Plan& p);
 int prepare_precision(Plan& p);   // function attributes of the precision-form kernels in use
 int64_t plan_gcd(int64_t a, int64_t b);
+// two-level W_Mt table (lo entries then hi entries, interleaved re, im) rounded to float once
+std::vector<float> twiddle_table_f32(int64_t Mt, int* bits, int* lo_n, int* hi_n);
 constexpr int kFoldMaxCluster = 16;   // largest cluster the fused kernel is launched with
 constexpr int kTuneMaxFold = 16;      // largest fold factor q the autotuner and default rule consider
 
@@ -204,6 +214,8 @@ int cuda_status_of(cudaError_t e);
 adfft_plan_s* ragged_create(const int64_t* N, const double* alpha, int64_t count, int dtype, int* err);
 int ragged_execute(Plan& p, const void* in, void* out, cudaStream_t s, int which);
 void ragged_release(Plan& p);
+int ragged_set_form(Plan& p, int form);              // ADFFT_RAGGED_CLASSES / ADFFT_RAGGED_QUEUE
+int ragged_queue_status(Plan& p, int* status);       // read and clear the queue kernel's status word
 
 // Two-pass second-pass launchers (twopass.cu).
 cudaError_t twopass_prepare(const TwoPassLaunch& L);

@@ -474,6 +474,11 @@ void release_twopass(Plan& p) {
 
 int64_t plan_gcd(int64_t a, int64_t b) { return gcd64(a, b); }
 
+std::vector<float> twiddle_table_f32(int64_t Mt, int* bits, int* lo_n, int* hi_n) {
+  *bits = (ilog2(Mt) + 1) / 2;
+  return build_two_level<float>(Mt, *bits, lo_n, hi_n);
+}
+
 namespace {
 
 // In-place iterative radix-2 FFT in double precision (host), forward sign.
@@ -992,6 +997,13 @@ int adfft_plan_set_algorithm(adfft_plan_t plan, int algo) {
   return ADFFT_OK;
 }
 
+int adfft_plan_set_ragged_form(adfft_plan_t plan, int form) {
+  using namespace adfft;
+  if (!plan || (form != ADFFT_RAGGED_CLASSES && form != ADFFT_RAGGED_QUEUE)) return ADFFT_ERR_INVALID_ARG;
+  if (!plan->p.ragged) return ADFFT_ERR_NOT_SUPPORTED;
+  return ragged_set_form(plan->p, form);
+}
+
 int adfft_plan_set_output(adfft_plan_t plan, int mode) {
   using namespace adfft;
   if (!plan || (mode != ADFFT_OUTPUT_FULL && mode != ADFFT_OUTPUT_HALF)) return ADFFT_ERR_INVALID_ARG;
@@ -1174,19 +1186,21 @@ int adfft_plan_sync_status(adfft_plan_t plan, void* stream) {
   Plan& p = plan->p;
   cudaStream_t s = (cudaStream_t)stream;
   if (p.ragged) {
-    // the shape classes' kernels report into their sub-plans' status words
+    // the shape classes' kernels report into their sub-plans' status words, the queue
+    // kernel into its own
     int rc = ADFFT_OK;
     for (auto* sp : p.r_sub) {
       const int r = adfft_plan_sync_status(sp, stream);
       if (rc == ADFFT_OK) rc = r;
     }
-    if (p.r_sub.empty()) {
-      const cudaError_t e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        return cuda_status(e);
-      }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
     }
+    int q = 0;
+    const int rq = ragged_queue_status(p, &q);
+    if (rc == ADFFT_OK) rc = rq != ADFFT_OK ? rq : (q != 0 ? ADFFT_ERR_TIMEOUT : ADFFT_OK);
     return rc;
   }
   int h = 0;

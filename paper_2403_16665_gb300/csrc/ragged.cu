@@ -22,6 +22,9 @@ namespace adfft {
 
 namespace {
 
+void release_queue(Plan& p);
+int launch_queue(Plan& p, const void* in, void* out, cudaStream_t s);
+
 void set_offsets(Plan& sub, const long long* d_offs) {
   sub.d_offs = d_offs;
   sub.fused.args.offs = d_offs;
@@ -55,6 +58,10 @@ int capture(Plan& p, const void* in, void* out, int which) {
     order.push_back({-(double)q.batch * (double)(q.M + q.N), i});
   }
   std::sort(order.begin(), order.end());
+  if (which == 0 && p.rq_on) {
+    rc = launch_queue(p, in, out, s0);
+    order.clear();
+  }
   for (size_t t = 0; t < order.size() && rc == ADFFT_OK; ++t) {
     Plan& q = p.r_sub[order[t].second]->p;
     cudaStream_t st = p.r_streams[t % kRaggedStreams];
@@ -92,6 +99,7 @@ void ragged_invalidate(Plan& p) { destroy_graphs(p); }
 
 void ragged_release(Plan& p) {
   destroy_graphs(p);
+  release_queue(p);
   for (auto* sp : p.r_sub) adfft_plan_destroy(sp);
   p.r_sub.clear();
   for (void* d : p.r_offs)
@@ -105,6 +113,242 @@ void ragged_release(Plan& p) {
   }
   if (p.r_fork) cudaEventDestroy(p.r_fork);
   p.r_fork = nullptr;
+}
+
+namespace {
+
+constexpr int kRqThreads = 512;
+constexpr int kRqTilePoints = 16384;        // complex points of U one tile holds in shared memory
+constexpr int kRqWholeGroupPoints = 8192;   // whole tiles take signals of a class up to this many points
+constexpr int kRqLeadersPerTile = 8192;     // leader bins of one unpack tile
+
+template <typename T>
+int rq_upload(Plan& p, const std::vector<T>& v, T** dst) {
+  void* d = nullptr;
+  const size_t bytes = std::max<size_t>(16, v.size() * sizeof(T));
+  cudaError_t e = cudaMalloc(&d, bytes);
+  if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (d) cudaFree(d);
+    return cuda_status_of(e);
+  }
+  p.rq_bufs.push_back(d);
+  *dst = static_cast<T*>(d);
+  return ADFFT_OK;
+}
+
+// Build the tile queue of the persistent form from the shape classes' fold geometry.
+// Returns ADFFT_OK (p.rq_ok set), ADFFT_ERR_UNSUPPORTED_SIZE when a class has no
+// single-CTA fold geometry (then only the class graph serves the plan), or an error.
+int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
+  const size_t ncls = p.r_sub.size();
+  std::vector<RqClass> cls(ncls);
+  std::vector<float> tables;
+  int tw_max = 0;
+  size_t buf_max = 0;
+  for (size_t c = 0; c < ncls; ++c) {
+    const Plan& q = p.r_sub[c]->p;
+    if (q.dbl) return ADFFT_ERR_UNSUPPORTED_SIZE;
+    // fold geometry of the class: packed real (even N and M) or complex input; the largest
+    // power-of-two sub-FFT dividing gcd(Mc, Nc) that one tile holds, with a fold of <= 64
+    int mode;
+    int64_t Nc, Mc;
+    core_shape(q, &mode, &Nc, &Mc);
+    if (mode != kLoadRealPacked && mode != kLoadComplex) return ADFFT_ERR_UNSUPPORTED_SIZE;
+    const int64_t gg = plan_gcd(Mc, Nc);
+    int64_t Np = gg & -gg;
+    while (Np > kRqTilePoints) Np /= 2;
+    if (Nc / Np > 64 || Mc >= (int64_t(1) << 30)) return ADFFT_ERR_UNSUPPORTED_SIZE;
+    RqClass& k = cls[c];
+    memset(&k, 0, sizeof(k));
+    k.Np = (int)Np;
+    k.logNp = 0;
+    while ((1 << k.logNp) < k.Np) ++k.logNp;
+    k.P = (int)(Mc / Np);
+    k.q = (int)(Nc / Np);
+    k.Nc = (int)Nc;
+    k.Mc = (int)Mc;
+    k.Mt = (int)(mode == kLoadRealPacked ? q.M : Mc);
+    k.region = k.Np + k.Np / 16 + 2;
+    int lr0 = (k.logNp == 0) ? 0 : (k.logNp % 4 ? k.logNp % 4 : 4);
+    if (lr0 == 1 && k.logNp >= 5) lr0 = 5;   // radix 2 merged with one radix-16 pass into radix 32
+    k.nrad = 1 + (k.logNp - lr0) / 4;
+    k.r0 = 1 << lr0;
+    k.real_packed = mode == kLoadRealPacked ? 1 : 0;
+    k.M = q.M;
+    k.scale = (float)q.scale;
+    k.divP = make_fastdiv((uint32_t)k.P);
+    int bits, lo_n, hi_n;
+    std::vector<float> t = twiddle_table_f32(k.Mt, &bits, &lo_n, &hi_n);
+    k.tw_bits = bits;
+    k.tw_lo_n = lo_n;
+    k.tw_hi_n = hi_n;
+    k.tw_off = (long long)(tables.size() / 2);
+    tables.insert(tables.end(), t.begin(), t.end());
+    tw_max = std::max(tw_max, lo_n + hi_n);
+    const int rpt = std::min(k.P, kRqTilePoints / k.Np);
+    buf_max = std::max(buf_max, (size_t)rpt * (size_t)k.region * 8);
+  }
+  const size_t smem = (((size_t)tw_max * 8 + 15) & ~size_t(15)) + buf_max;
+  if (smem > 200 * 1024) return ADFFT_ERR_UNSUPPORTED_SIZE;
+
+  // signals and tiles: split signals (residues beyond one tile) largest first, each signal's
+  // fft tiles followed by the unpack tiles of the split signal before it; then the whole
+  // tiles of each class, classes with the most work first
+  std::vector<RqSignal> sigs((size_t)p.r_count);
+  std::vector<RqTile> tiles;
+  std::vector<int> whole;
+  std::vector<std::pair<int64_t, int64_t>> split;   // (-M, signal)
+  std::vector<int> cls_of((size_t)p.r_count, -1);
+  for (size_t c = 0; c < ncls; ++c)
+    for (int64_t s : members[c]) cls_of[(size_t)s] = (int)c;
+  long long scratch = 0;
+  for (int64_t s = 0; s < p.r_count; ++s) {
+    RqSignal& g = sigs[(size_t)s];
+    memset(&g, 0, sizeof(g));
+    g.in_bytes = p.r_in_off[(size_t)s] * (long long)p.in_elem;
+    g.out_bin = p.r_out_off[(size_t)s];
+    const RqClass& k = cls[(size_t)cls_of[(size_t)s]];
+    if ((int64_t)k.P * k.Np > kRqTilePoints) {
+      g.scratch = scratch;
+      scratch += (long long)k.P * k.Np;
+      const int rpt = std::min(k.P, kRqTilePoints / k.Np);
+      g.nfft = (k.P + rpt - 1) / rpt;
+      split.push_back({-k.M, s});
+    }
+  }
+  std::sort(split.begin(), split.end());
+  auto unpack_tiles = [&](int64_t s) {
+    const int c = cls_of[(size_t)s];
+    const RqClass& k = cls[(size_t)c];
+    const int jt = k.real_packed ? k.Mc / 2 + 1 : k.Mc;
+    for (int j0 = 0; j0 < jt; j0 += kRqLeadersPerTile)
+      tiles.push_back(RqTile{kRqUnpack, c, (int)s, j0, std::min(jt, j0 + kRqLeadersPerTile), 0});
+  };
+  for (size_t i = 0; i < split.size(); ++i) {
+    const int64_t s = split[i].second;
+    const int c = cls_of[(size_t)s];
+    const RqClass& k = cls[(size_t)c];
+    const int rpt = std::min(k.P, kRqTilePoints / k.Np);
+    for (int r = 0; r < k.P; r += rpt) tiles.push_back(RqTile{kRqFft, c, (int)s, r, std::min(rpt, k.P - r), 0});
+    if (i > 0) unpack_tiles(split[i - 1].second);
+  }
+  if (!split.empty()) unpack_tiles(split.back().second);
+  std::vector<std::pair<int64_t, size_t>> corder;
+  for (size_t c = 0; c < ncls; ++c) {
+    const RqClass& k = cls[c];
+    if ((int64_t)k.P * k.Np > kRqTilePoints) continue;
+    corder.push_back({-(int64_t)members[c].size() * (k.M + p.r_sub[c]->p.N), c});
+  }
+  std::sort(corder.begin(), corder.end());
+  for (auto& co : corder) {
+    const size_t c = co.second;
+    const RqClass& k = cls[c];
+    const int per = std::max(1, kRqWholeGroupPoints / (k.P * k.Np));
+    for (size_t i = 0; i < members[c].size(); i += per) {
+      const int cnt = (int)std::min<size_t>(per, members[c].size() - i);
+      tiles.push_back(RqTile{kRqWhole, (int)c, (int)whole.size(), 0, cnt, 0});
+      for (int w = 0; w < cnt; ++w) whole.push_back((int)members[c][i + w]);
+    }
+  }
+  if (tiles.size() > 0x7fffffff || p.r_count > 0x7ffffffe) return ADFFT_ERR_UNSUPPORTED_SIZE;
+
+  RqArgs& a = p.rq;
+  memset(&a, 0, sizeof(a));
+  RqTile* d_tiles = nullptr;
+  RqClass* d_cls = nullptr;
+  RqSignal* d_sigs = nullptr;
+  int* d_whole = nullptr;
+  float* d_tab = nullptr;
+  int rc;
+  if ((rc = rq_upload(p, tiles, &d_tiles)) != ADFFT_OK) return rc;
+  if ((rc = rq_upload(p, cls, &d_cls)) != ADFFT_OK) return rc;
+  if ((rc = rq_upload(p, sigs, &d_sigs)) != ADFFT_OK) return rc;
+  if ((rc = rq_upload(p, whole, &d_whole)) != ADFFT_OK) return rc;
+  if ((rc = rq_upload(p, tables, &d_tab)) != ADFFT_OK) return rc;
+  void* d_scr = nullptr;
+  void* d_cnt = nullptr;
+  void* d_st = nullptr;
+  cudaError_t e = cudaMalloc(&d_scr, std::max<size_t>(16, (size_t)scratch * 8));
+  if (e == cudaSuccess) p.rq_bufs.push_back(d_scr);
+  if (e == cudaSuccess) e = cudaMalloc(&d_cnt, (size_t)(p.r_count + 1) * sizeof(int));
+  if (e == cudaSuccess) p.rq_bufs.push_back(d_cnt);
+  if (e == cudaSuccess) e = cudaMalloc(&d_st, sizeof(int));
+  if (e == cudaSuccess) p.rq_bufs.push_back(d_st);
+  if (e == cudaSuccess) e = cudaMemset(d_st, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status_of(e);
+  }
+  a.tiles = d_tiles;
+  a.ntiles = (int)tiles.size();
+  a.classes = d_cls;
+  a.sigs = d_sigs;
+  a.whole_sigs = d_whole;
+  a.tables = reinterpret_cast<const float2*>(d_tab);
+  a.scratch = static_cast<float2*>(d_scr);
+  a.counters = static_cast<int*>(d_cnt);
+  a.status = static_cast<int*>(d_st);
+  a.tw_max = tw_max;
+  a.wait_limit = kWaitLimitCycles;
+  p.rq_smem = smem;
+  e = cudaFuncSetAttribute(ragged_queue_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ragged_queue_kernel<0>, kRqThreads, smem);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return ADFFT_ERR_UNSUPPORTED_SIZE;
+  }
+  // every CTA resident at once: a CTA waiting in an unpack tile never waits for one that
+  // has not started
+  p.rq_grid = std::max(1, std::min(per_sm * sms, (int)tiles.size()));
+  p.rq_ok = true;
+  return ADFFT_OK;
+}
+
+void release_queue(Plan& p) {
+  for (void* d : p.rq_bufs)
+    if (d) cudaFree(d);
+  p.rq_bufs.clear();
+  p.rq_ok = p.rq_on = false;
+}
+
+int launch_queue(Plan& p, const void* in, void* out, cudaStream_t s) {
+  RqArgs a = p.rq;
+  a.in = in;
+  a.out = out;
+  cudaError_t e = cudaMemsetAsync(a.counters, 0, (size_t)(p.r_count + 1) * sizeof(int), s);
+  if (e == cudaSuccess) {
+    ragged_queue_kernel<0><<<p.rq_grid, kRqThreads, p.rq_smem, s>>>(a);
+    e = cudaGetLastError();
+  }
+  return cuda_status_of(e);
+}
+
+}  // namespace
+
+int ragged_set_form(Plan& p, int form) {
+  if (form == ADFFT_RAGGED_QUEUE && !p.rq_ok) return ADFFT_ERR_NOT_SUPPORTED;
+  const bool on = form == ADFFT_RAGGED_QUEUE;
+  if (on != p.rq_on) {
+    p.rq_on = on;
+    destroy_graphs(p);
+  }
+  return ADFFT_OK;
+}
+
+int ragged_queue_status(Plan& p, int* status) {
+  *status = 0;
+  if (!p.rq_ok) return ADFFT_OK;
+  cudaError_t e = cudaMemcpy(status, p.rq.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && *status != 0) e = cudaMemset(p.rq.status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status_of(e);
+  }
+  return ADFFT_OK;
 }
 
 adfft_plan_s* ragged_create(const int64_t* N, const double* alpha, int64_t count, int dtype, int* err) {
@@ -155,6 +399,17 @@ adfft_plan_s* ragged_create(const int64_t* N, const double* alpha, int64_t count
     p.r_in_off[(size_t)i + 1] = p.r_in_off[(size_t)i] + N[i];
     p.r_out_off[(size_t)i + 1] = p.r_out_off[(size_t)i] + Ms[(size_t)i];
   }
+  // packed real classes read their samples in pairs (8-byte loads): a real signal with even N
+  // and M must start at an even sample offset
+  if (p.real) {
+    for (int64_t i = 0; i < count; ++i) {
+      if (N[i] % 2 == 0 && Ms[(size_t)i] % 2 == 0 && (p.r_in_off[(size_t)i] % 2) != 0) {
+        delete h;
+        *err = ADFFT_ERR_NOT_SUPPORTED;
+        return nullptr;
+      }
+    }
+  }
   // the packed buffers, as one "signal" for the size and overlap checks
   p.batch = 1;
   p.N = p.r_in_off[(size_t)count];
@@ -172,6 +427,8 @@ adfft_plan_s* ragged_create(const int64_t* N, const double* alpha, int64_t count
   // shape classes
   std::map<std::pair<int64_t, int64_t>, std::vector<int64_t>> classes;
   for (int64_t i = 0; i < count; ++i) classes[{N[i], Ms[(size_t)i]}].push_back(i);
+  std::vector<std::vector<int64_t>> members;
+  for (auto& kv : classes) members.push_back(kv.second);
   for (auto& kv : classes) {
     const int64_t n = kv.first.first, m = kv.first.second;
     const std::vector<int64_t>& members = kv.second;
@@ -218,14 +475,24 @@ adfft_plan_s* ragged_create(const int64_t* N, const double* alpha, int64_t count
     cudaGetLastError();
     return bail(ADFFT_ERR_CUDA);
   }
+  // the persistent queue form, where every class has a single-CTA fold geometry
+  if (count > 0) {
+    const int rc = build_queue(p, members);
+    if (rc != ADFFT_OK && rc != ADFFT_ERR_UNSUPPORTED_SIZE) return bail(rc);
+    if (rc != ADFFT_OK) release_queue(p);
+  }
   return h;
 }
 
 int ragged_execute(Plan& p, const void* in, void* out, cudaStream_t s, int which) {
   if (p.r_count == 0) return ADFFT_OK;
   if (which == 1) {
-    for (auto* sp : p.r_sub)
-      if (!sp->p.fold_ok && !sp->p.tp_ok) return ADFFT_ERR_NOT_SUPPORTED;
+    // chirp-z classes set up their adjoint's tables (device allocations) outside the capture
+    for (auto* sp : p.r_sub) {
+      if (sp->p.fold_ok || sp->p.tp_ok) continue;
+      const int rc = setup_bluestein_adjoint(sp->p);
+      if (rc != ADFFT_OK) return rc == ADFFT_ERR_UNSUPPORTED_SIZE ? ADFFT_ERR_NOT_SUPPORTED : rc;
+    }
   }
   if (!p.r_graph[which] || p.r_graph_in[which] != in || p.r_graph_out[which] != out) {
     int rc = capture(p, in, out, which);

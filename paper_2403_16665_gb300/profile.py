@@ -153,6 +153,18 @@ def ragged(args):
               % (len(Ns), name, ms, gbs, frac, points / ms * 1e3))
 
     report("ragged plan, forward", _time(lambda: plan.execute(x.data_ptr(), X.data_ptr()), args.iters))
+    try:
+        plan.set_form(adfft.RAGGED_QUEUE)
+        Xq = torch.empty_like(X)
+        report("ragged plan, forward, queue form", _time(lambda: plan.execute(x.data_ptr(), Xq.data_ptr()), args.iters))
+        plan.set_form(adfft.RAGGED_CLASSES)
+        plan.execute(x.data_ptr(), X.data_ptr())
+        torch.cuda.synchronize()
+        print("queue form vs class graph: rel difference %.2e"
+              % (torch.linalg.norm(Xq - X) / torch.linalg.norm(X)).item())
+        del Xq
+    except adfft.AdfftError as e:
+        print("queue form not available:", e)
     report("ragged plan, adjoint", _time(lambda: plan.execute_adjoint(g.data_ptr(), xb.data_ptr()), args.iters))
     Xr = X.clone()
     if args.tune:

@@ -189,3 +189,78 @@ def test_ragged_c5_fp32_gradient_directional_difference():
         fd = (loss(x + eps * d) - loss(x - eps * d)) / (2 * eps)
         an = (grad.double() * d.double()).sum().item()
         assert abs(fd - an) <= 1e-4 * abs(an), (fd, an)
+
+
+@pytest.mark.parametrize("code,seed,count", [(adfft.R32, 11, 60), (adfft.C64, 12, 40), (adfft.R32, 13, 300)])
+def test_ragged_queue_form_matches_class_graph(code, seed, count):
+    """The persistent queue form (whole / fft / unpack tiles) against the class-graph form at
+    every bin and against the oracle on sampled bins of one signal per class; mixes include
+    N = 65536 signals (split into fft and unpack tiles)."""
+    torch = _torch()
+    rng = np.random.default_rng(seed)
+    Ns = [int(2 ** e) for e in rng.integers(8, 17, size=count)] + [65536, 65536, 256]
+    alphas = list(rng.choice([2.0, 3.0, 4.0, 8.0, 2.5], size=len(Ns) - 3)) + [8.0, 2.5, 2.0]
+    plan = adfft.RaggedPlan(Ns, alphas, code)
+    dev = torch.device("cuda:0")
+    ni, no = int(plan.in_off[-1]), int(plan.out_off[-1])
+    x = torch.randn(ni, device=dev) if code == adfft.R32 else torch.randn(ni, dtype=torch.complex64, device=dev)
+    Xg = torch.empty(no, dtype=torch.complex64, device=dev)
+    plan.set_form(adfft.RAGGED_CLASSES)
+    plan.execute(x.data_ptr(), Xg.data_ptr())
+    plan.sync_status()
+    plan.set_form(adfft.RAGGED_QUEUE)
+    Xq = torch.full((no,), complex(float("nan"), float("nan")), dtype=torch.complex64, device=dev)
+    for _ in range(2):   # the second execute replays the captured graph (counters reset inside)
+        plan.execute(x.data_ptr(), Xq.data_ptr())
+        plan.sync_status()
+    assert torch.isfinite(Xq.view(torch.float32)).all().item()
+    assert (torch.linalg.vector_norm(Xq - Xg) / torch.linalg.vector_norm(Xg)).item() <= 1e-6
+    xs = x.cpu().numpy()
+    seen = set()
+    for i, (N, a) in enumerate(zip(Ns, alphas)):
+        M = int(round(a * N))
+        if (N, M) in seen:
+            continue
+        seen.add((N, M))
+        bins = np.unique(np.concatenate([[0, M // 2, M - 1], rng.integers(0, M, 64)]))
+        xi = xs[plan.in_off[i]:plan.in_off[i + 1]]
+        ref = oracle.alpha_dft(xi.astype(np.complex128 if code == adfft.C64 else np.float64), M, bins=bins)
+        got = Xq[int(plan.out_off[i]):int(plan.out_off[i + 1])][torch.from_numpy(bins).to(dev)].cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-6 * np.log2(M), (N, M)
+
+
+def test_ragged_queue_form_c5_every_class():
+    """The 10000-signal workload through the queue form: every bin against the class graph,
+    and one signal per shape class against the oracle on sampled bins."""
+    torch = _torch()
+    x_np, Ns, alphas, plan = _c5_plan(torch)
+    Ms = np.rint(alphas * Ns).astype(np.int64)
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(x_np).to(dev)
+    no = int(plan.out_off[-1])
+    Xg = torch.empty(no, dtype=torch.complex64, device=dev)
+    plan.set_form(adfft.RAGGED_CLASSES)
+    plan.execute(x.data_ptr(), Xg.data_ptr())
+    plan.set_form(adfft.RAGGED_QUEUE)
+    Xq = torch.empty(no, dtype=torch.complex64, device=dev)
+    plan.execute(x.data_ptr(), Xq.data_ptr())
+    plan.sync_status()
+    assert (torch.linalg.vector_norm(Xq - Xg) / torch.linalg.vector_norm(Xg)).item() <= 1e-6
+    rng = np.random.default_rng(8)
+    first = {}
+    for i, key in enumerate(zip(Ns.tolist(), Ms.tolist())):
+        first.setdefault(key, i)
+    for (N, M), i in sorted(first.items()):
+        bins = np.unique(np.concatenate([[0, M // 2, M - 1], rng.integers(0, M, 48)]))
+        ref = oracle.alpha_dft(x_np[plan.in_off[i]:plan.in_off[i + 1]].astype(np.float64), M, bins=bins)
+        got = Xq[int(plan.out_off[i]):int(plan.out_off[i + 1])][torch.from_numpy(bins).to(dev)].cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-6 * np.log2(M), (N, M)
+
+
+def test_ragged_queue_form_refused_where_unavailable():
+    _torch()
+    plan = adfft.RaggedPlan([1000, 2000], [2.5, 2.5], adfft.C64)   # chirp-z classes: no fold geometry
+    with pytest.raises(adfft.AdfftError):
+        plan.set_form(adfft.RAGGED_QUEUE)
+    with pytest.raises(adfft.AdfftError):
+        adfft.RaggedPlan([3, 4], [2.0, 2.0], adfft.R32)             # even-N signal at an odd offset
