@@ -166,17 +166,17 @@ typedef enum {
 /*
  * Choose how a ragged plan's forward transform runs.  ADFFT_RAGGED_QUEUE: one persistent
  * kernel (as many CTAs as are resident) takes tiles from a queue in order: a "whole" tile
- * transforms signals whose residue FFTs fit one CTA's shared memory (several signals of a
- * class in turn); a longer signal is split into "fft" tiles (a group of its residues, the
+ * transforms signals whose residue FFTs fit one CTA's shared memory (up to 64 signals of a
+ * class side by side); a longer signal is split into "fft" tiles (a group of its residues, the
  * sub-FFT results written to plan workspace) followed in the queue by "unpack" tiles (a
- * range of its output bins, gathered from that workspace once its fft tiles are counted;
- * the wait is bounded).  The execute is a memset of the queue counters plus that launch,
+ * range of its output bins, gathered from that workspace once its fft tiles are counted,
+ * queued about one wave of resident CTAs after them; the wait is bounded).  The execute is a memset of the queue counters plus that launch,
  * captured in a CUDA graph like the other form.  Served when every shape class is FP32 or
  * complex64 with even N and M for real input (packed) and a fold of at most 64 blocks onto
- * a power-of-two sub-FFT of at most 16384 points dividing its length and bin count; plan
+ * a power-of-two sub-FFT of at most 4096 points dividing its length and bin count; plan
  * workspace = 8 bytes per packed bin of the split signals (those whose residue FFTs exceed
- * 16384 points).  ADFFT_ERR_NOT_SUPPORTED for
- * plans it cannot serve or non-ragged plans.  The adjoint always uses the class graph.
+ * 4096 points).  ADFFT_ERR_NOT_SUPPORTED for plans it cannot serve or non-ragged plans.
+ * The adjoint always uses the class graph.
  */
 int adfft_plan_set_ragged_form(adfft_plan_t plan, int form);
 

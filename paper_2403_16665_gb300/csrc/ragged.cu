@@ -117,9 +117,11 @@ void ragged_release(Plan& p) {
 
 namespace {
 
-constexpr int kRqThreads = 512;
-constexpr int kRqTilePoints = 16384;        // complex points of U one tile holds in shared memory
-constexpr int kRqWholeGroupPoints = 8192;   // whole tiles take signals of a class up to this many points
+// Small tiles: 4096 points and 128 threads give 4 independent CTAs per SM (shared memory
+// and registers both allow 4), which hides the latency of each CTA's fold / pass / store
+// phases behind the others better than one 512-thread CTA with 16384 points.
+constexpr int kRqThreads = 128;
+constexpr int kRqTilePoints = 4096;         // complex points of U one tile holds in shared memory
 constexpr int kRqLeadersPerTile = 8192;     // leader bins of one unpack tile
 
 template <typename T>
@@ -136,6 +138,11 @@ int rq_upload(Plan& p, const std::vector<T>& v, T** dst) {
   p.rq_bufs.push_back(d);
   *dst = static_cast<T*>(d);
   return ADFFT_OK;
+}
+
+// signals of a class that one whole tile transforms side by side
+int whole_group(const RqClass& k) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kRqMaxGroup, kRqTilePoints / ((int64_t)k.P * k.Np)));
 }
 
 // Build the tile queue of the persistent form from the shape classes' fold geometry.
@@ -187,11 +194,24 @@ int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
     k.tw_off = (long long)(tables.size() / 2);
     tables.insert(tables.end(), t.begin(), t.end());
     tw_max = std::max(tw_max, lo_n + hi_n);
-    const int rpt = std::min(k.P, kRqTilePoints / k.Np);
+    // regions a tile holds: R of the residues of a split signal, or the P residues of each
+    // signal of a whole tile
+    const int rpt = (int64_t)k.P * k.Np > kRqTilePoints ? std::min(k.P, kRqTilePoints / k.Np)
+                                                        : whole_group(k) * k.P;
     buf_max = std::max(buf_max, (size_t)rpt * (size_t)k.region * 8);
   }
   const size_t smem = (((size_t)tw_max * 8 + 15) & ~size_t(15)) + buf_max;
   if (smem > 200 * 1024) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  cudaError_t e = cudaFuncSetAttribute(ragged_queue_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ragged_queue_kernel<0>, kRqThreads, smem);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return ADFFT_ERR_UNSUPPORTED_SIZE;
+  }
+  const int resident = per_sm * sms;
+  const int lag = resident;
 
   // signals and tiles: split signals (residues beyond one tile) largest first, each signal's
   // fft tiles followed by the unpack tiles of the split signal before it; then the whole
@@ -226,15 +246,20 @@ int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
     for (int j0 = 0; j0 < jt; j0 += kRqLeadersPerTile)
       tiles.push_back(RqTile{kRqUnpack, c, (int)s, j0, std::min(jt, j0 + kRqLeadersPerTile), 0});
   };
+  // a signal's unpack tiles follow its last fft tile by at least `lag` fft tiles (about one
+  // wave of resident CTAs), so that an unpack tile seldom waits for fft tiles still running
+  std::vector<std::pair<size_t, int64_t>> pending;   // (tiles emitted after its fft tiles, signal)
+  size_t next = 0;
   for (size_t i = 0; i < split.size(); ++i) {
     const int64_t s = split[i].second;
     const int c = cls_of[(size_t)s];
     const RqClass& k = cls[(size_t)c];
     const int rpt = std::min(k.P, kRqTilePoints / k.Np);
     for (int r = 0; r < k.P; r += rpt) tiles.push_back(RqTile{kRqFft, c, (int)s, r, std::min(rpt, k.P - r), 0});
-    if (i > 0) unpack_tiles(split[i - 1].second);
+    pending.push_back({tiles.size(), s});
+    while (next < pending.size() && pending[next].first + (size_t)lag <= tiles.size()) unpack_tiles(pending[next++].second);
   }
-  if (!split.empty()) unpack_tiles(split.back().second);
+  while (next < pending.size()) unpack_tiles(pending[next++].second);
   std::vector<std::pair<int64_t, size_t>> corder;
   for (size_t c = 0; c < ncls; ++c) {
     const RqClass& k = cls[c];
@@ -245,7 +270,7 @@ int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
   for (auto& co : corder) {
     const size_t c = co.second;
     const RqClass& k = cls[c];
-    const int per = std::max(1, kRqWholeGroupPoints / (k.P * k.Np));
+    const int per = whole_group(k);
     for (size_t i = 0; i < members[c].size(); i += per) {
       const int cnt = (int)std::min<size_t>(per, members[c].size() - i);
       tiles.push_back(RqTile{kRqWhole, (int)c, (int)whole.size(), 0, cnt, 0});
@@ -270,7 +295,7 @@ int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
   void* d_scr = nullptr;
   void* d_cnt = nullptr;
   void* d_st = nullptr;
-  cudaError_t e = cudaMalloc(&d_scr, std::max<size_t>(16, (size_t)scratch * 8));
+  e = cudaMalloc(&d_scr, std::max<size_t>(16, (size_t)scratch * 8));
   if (e == cudaSuccess) p.rq_bufs.push_back(d_scr);
   if (e == cudaSuccess) e = cudaMalloc(&d_cnt, (size_t)(p.r_count + 1) * sizeof(int));
   if (e == cudaSuccess) p.rq_bufs.push_back(d_cnt);
@@ -293,17 +318,9 @@ int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
   a.tw_max = tw_max;
   a.wait_limit = kWaitLimitCycles;
   p.rq_smem = smem;
-  e = cudaFuncSetAttribute(ragged_queue_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0, sms = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ragged_queue_kernel<0>, kRqThreads, smem);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-  if (e != cudaSuccess || per_sm < 1) {
-    cudaGetLastError();
-    return ADFFT_ERR_UNSUPPORTED_SIZE;
-  }
   // every CTA resident at once: a CTA waiting in an unpack tile never waits for one that
   // has not started
-  p.rq_grid = std::max(1, std::min(per_sm * sms, (int)tiles.size()));
+  p.rq_grid = std::max(1, std::min(resident, (int)tiles.size()));
   p.rq_ok = true;
   return ADFFT_OK;
 }

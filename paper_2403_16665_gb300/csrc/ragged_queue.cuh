@@ -8,8 +8,9 @@
 // shape class (Np, P, q, Mc, twiddle table) and is served by tiles of three kinds:
 //
 //   whole   the signal's P residue FFTs fit one CTA: fold, FFT and unpack in shared
-//           memory, natural-order stores (a tile may take several signals of its class
-//           in turn);
+//           memory, natural-order stores (a tile takes up to 64 signals of its class side
+//           by side: one fold per signal, then the Stockham passes and the unpacking over
+//           all of them);
 //   fft     R of the P residues of a longer signal: fold and FFT in shared memory, U_r
 //           written to a global scratch area (residue-major, coalesced), then the
 //           signal's counter is raised (release);
@@ -39,6 +40,7 @@ struct RqClass {
 };
 
 enum RqTileKind : int { kRqWhole = 0, kRqFft = 1, kRqUnpack = 2 };
+constexpr int kRqMaxGroup = 64;   // signals of one whole tile at most
 
 struct RqTile {
   int kind, cls;
@@ -95,14 +97,20 @@ __device__ __forceinline__ FusedArgs rq_fused_args(const RqClass& c, int rpc) {
   return a;
 }
 
-// fold + twiddle + FFT of residues [r0, r0 + rpc) of one signal into buf
+// fold + twiddle + first radix of residues [r0, r0 + rpc) of one signal into buf
 template <int R0>
-__device__ __forceinline__ void rq_fft(const FusedArgs& a, const void* u, int mode, float2* buf,
-                                       const TwTable<float2>& tab, int r0) {
-  constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : R0 == 16 ? 4 : 5;
+__device__ __forceinline__ void rq_first(const FusedArgs& a, const void* u, int mode, float2* buf,
+                                         const TwTable<float2>& tab, int r0) {
   first_pass<R0, float2, false, RuntimeShape>(a, u, nullptr, mode, buf, tab, r0);
-  __syncthreads();
+}
+
+// the radix-16 Stockham passes over all a.RPC regions of buf (after the first pass of radix R0);
+// starts and ends with the CTA synchronised (every pass ends with a barrier)
+template <int R0>
+__device__ __forceinline__ void rq_passes(const FusedArgs& a, float2* buf, const TwTable<float2>& tab) {
+  constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : R0 == 16 ? 4 : 5;
   int Ns = R0, logNs = LOGR0;
+  __syncthreads();
   for (int p = 1; p < a.nrad; ++p) {
     stockham_pass<16, 32, float2, RuntimeShape>(a, buf, tab, Ns, logNs);
     Ns <<= 4;
@@ -110,47 +118,62 @@ __device__ __forceinline__ void rq_fft(const FusedArgs& a, const void* u, int mo
   }
 }
 
-__device__ __forceinline__ void rq_fft_any(const FusedArgs& a, int r0radix, const void* u, int mode, float2* buf,
-                                           const TwTable<float2>& tab, int r0) {
+__device__ __forceinline__ void rq_first_any(const FusedArgs& a, int r0radix, const void* u, int mode, float2* buf,
+                                             const TwTable<float2>& tab, int r0) {
   switch (r0radix) {
-    case 1: rq_fft<1>(a, u, mode, buf, tab, r0); break;
-    case 2: rq_fft<2>(a, u, mode, buf, tab, r0); break;
-    case 4: rq_fft<4>(a, u, mode, buf, tab, r0); break;
-    case 8: rq_fft<8>(a, u, mode, buf, tab, r0); break;
-    case 16: rq_fft<16>(a, u, mode, buf, tab, r0); break;
-    default: rq_fft<32>(a, u, mode, buf, tab, r0); break;
+    case 1: rq_first<1>(a, u, mode, buf, tab, r0); break;
+    case 2: rq_first<2>(a, u, mode, buf, tab, r0); break;
+    case 4: rq_first<4>(a, u, mode, buf, tab, r0); break;
+    case 8: rq_first<8>(a, u, mode, buf, tab, r0); break;
+    case 16: rq_first<16>(a, u, mode, buf, tab, r0); break;
+    default: rq_first<32>(a, u, mode, buf, tab, r0); break;
   }
 }
 
-// Unpack leaders j in [j0, j1) (packed real: j <= Mc/2; complex: j < Mc) of one signal, with
-// U fetched by `getU(q)` (q = bin of the complex core), and store natural-order bins.
-template <class GetU>
-__device__ __forceinline__ void rq_unpack(const RqClass& c, const TwTable<float2>& tab, float2* out, unsigned j0,
-                                          unsigned j1, GetU getU) {
+__device__ __forceinline__ void rq_passes_any(const FusedArgs& a, int r0radix, float2* buf,
+                                              const TwTable<float2>& tab) {
+  switch (r0radix) {
+    case 1: rq_passes<1>(a, buf, tab); break;
+    case 2: rq_passes<2>(a, buf, tab); break;
+    case 4: rq_passes<4>(a, buf, tab); break;
+    case 8: rq_passes<8>(a, buf, tab); break;
+    case 16: rq_passes<16>(a, buf, tab); break;
+    default: rq_passes<32>(a, buf, tab); break;
+  }
+}
+
+// Unpack leader j (packed real: j <= Mc/2; complex: j < Mc) of one signal, with U fetched
+// by `getU(q)` (q = bin of the complex core), and store its natural-order bins.
+// (packed real: Uj = U_j and Up = U_{Mc - j}; complex: Uj = U_j, Up unused)
+__device__ __forceinline__ void rq_unpack_vals(const RqClass& c, const TwTable<float2>& tab, float2* out,
+                                               unsigned j, float2 Uj, float2 Up) {
   const unsigned Mc = (unsigned)c.Mc;
   const float S = c.scale;
   if (c.real_packed) {
     const float hS = 0.5f * S;
-    for (unsigned j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-      const float2 Uj = getU(j);
-      const float2 Up = getU(j ? Mc - j : 0u);
-      const float2 A = cadd(Uj, cconj(Up));
-      const float2 B = csub(Uj, cconj(Up));
-      float2 wn = tab(j);
-      wn = cmake<float2>(hS * wn.y, -hS * wn.x);   // (S/2)(-i) W_M^j
-      const float2 t = cmul(wn, B);
-      const float2 hA = cscale(A, hS);
-      const float2 X1 = cadd(hA, t), X2 = csub(hA, t);
-      st_stream(out + j, X1);
-      st_stream(out + j + Mc, X2);
-      if (j != 0 && 2 * j != Mc) {
-        st_stream(out + (Mc - j), cconj(X2));
-        st_stream(out + ((unsigned long long)c.M - j), cconj(X1));
-      }
+    const float2 A = cadd(Uj, cconj(Up));
+    const float2 B = csub(Uj, cconj(Up));
+    float2 wn = tab(j);
+    wn = cmake<float2>(hS * wn.y, -hS * wn.x);   // (S/2)(-i) W_M^j
+    const float2 t = cmul(wn, B);
+    const float2 hA = cscale(A, hS);
+    const float2 X1 = cadd(hA, t), X2 = csub(hA, t);
+    st_stream(out + j, X1);
+    st_stream(out + j + Mc, X2);
+    if (j != 0 && 2 * j != Mc) {
+      st_stream(out + (Mc - j), cconj(X2));
+      st_stream(out + ((unsigned long long)c.M - j), cconj(X1));
     }
   } else {
-    for (unsigned j = j0 + threadIdx.x; j < j1; j += blockDim.x) st_stream(out + j, cscale(getU(j), S));
+    st_stream(out + j, cscale(Uj, S));
   }
+}
+
+template <class GetU>
+__device__ __forceinline__ void rq_unpack_one(const RqClass& c, const TwTable<float2>& tab, float2* out,
+                                              unsigned j, GetU getU) {
+  const unsigned Mc = (unsigned)c.Mc;
+  rq_unpack_vals(c, tab, out, j, getU(j), c.real_packed ? getU(j ? Mc - j : 0u) : czero<float2>());
 }
 
 // (a template so that only the translation unit that launches it instantiates it)
@@ -160,6 +183,7 @@ __global__ void __launch_bounds__(512) ragged_queue_kernel(const RqArgs g) {
   float2* tw_s = reinterpret_cast<float2*>(smem_raw);
   float2* buf = reinterpret_cast<float2*>(smem_raw + ((g.tw_max * 8 + 15) & ~15));
   __shared__ int s_tile, s_fail;
+  __shared__ long long s_out[kRqMaxGroup];   // first output bin of each signal of a whole tile
   int cached_cls = -1;
   if (threadIdx.x == 0) s_fail = 0;
   for (;;) {
@@ -179,24 +203,33 @@ __global__ void __launch_bounds__(512) ragged_queue_kernel(const RqArgs g) {
     const TwTable<float2> tab{tw_s, tw_s + c.tw_lo_n, c.tw_bits, (1u << c.tw_bits) - 1u};
     const int mode = c.real_packed ? kLoadRealPacked : kLoadComplex;
     if (t.kind == kRqWhole) {
-      const FusedArgs a = rq_fused_args(c, c.P);
-      for (int w = 0; w < t.a1; ++w) {
+      // the t.a1 signals of the group side by side: signal w in regions [w P, (w + 1) P)
+      const int nw = t.a1;
+      const FusedArgs a1 = rq_fused_args(c, c.P);
+      for (int w = threadIdx.x; w < nw; w += blockDim.x) s_out[w] = g.sigs[g.whole_sigs[t.sig + w]].out_bin;
+      for (int w = 0; w < nw; ++w) {
         const RqSignal sg = g.sigs[g.whole_sigs[t.sig + w]];
         const void* u = reinterpret_cast<const unsigned char*>(g.in) + sg.in_bytes;
-        rq_fft_any(a, c.r0, u, mode, buf, tab, 0);
-        const unsigned jt = c.real_packed ? (unsigned)c.Mc / 2 + 1 : (unsigned)c.Mc;
-        float2* out = reinterpret_cast<float2*>(g.out) + sg.out_bin;
-        rq_unpack(c, tab, out, 0u, jt, [&](unsigned q) {
+        rq_first_any(a1, c.r0, u, mode, buf + (size_t)w * c.P * c.region, tab, 0);
+      }
+      rq_passes_any(rq_fused_args(c, nw * c.P), c.r0, buf, tab);
+      const unsigned jt = c.real_packed ? (unsigned)c.Mc / 2 + 1 : (unsigned)c.Mc;
+      const unsigned total = (unsigned)nw * jt;
+      for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
+        const unsigned w = i / jt, j = i - w * jt;
+        const float2* bw = buf + (size_t)w * c.P * c.region;
+        float2* out = reinterpret_cast<float2*>(g.out) + s_out[w];
+        rq_unpack_one(c, tab, out, j, [&](unsigned q) {
           const unsigned k = fdiv(q, c.divP);
-          return buf[(q - k * (unsigned)c.P) * (unsigned)c.region + (unsigned)pad16((int)k)];
+          return bw[(q - k * (unsigned)c.P) * (unsigned)c.region + (unsigned)pad16((int)k)];
         });
-        __syncthreads();
       }
     } else if (t.kind == kRqFft) {
       const FusedArgs a = rq_fused_args(c, t.a1);
       const RqSignal sg = g.sigs[t.sig];
       const void* u = reinterpret_cast<const unsigned char*>(g.in) + sg.in_bytes;
-      rq_fft_any(a, c.r0, u, mode, buf, tab, t.a0);
+      rq_first_any(a, c.r0, u, mode, buf, tab, t.a0);
+      rq_passes_any(a, c.r0, buf, tab);
       // U_r[k] of residues a0 .. a0 + a1 - 1 to the scratch, residue-major
       float2* dst = g.scratch + sg.scratch + (long long)t.a0 * c.Np;
       const unsigned total = (unsigned)t.a1 * (unsigned)c.Np;
@@ -223,10 +256,11 @@ __global__ void __launch_bounds__(512) ragged_queue_kernel(const RqArgs g) {
       if (s_fail) break;
       const float2* U = g.scratch + sg.scratch;
       float2* out = reinterpret_cast<float2*>(g.out) + sg.out_bin;
-      rq_unpack(c, tab, out, (unsigned)t.a0, (unsigned)t.a1, [&](unsigned q) {
-        const unsigned k = fdiv(q, c.divP);
-        return __ldcg(U + (long long)(q - k * (unsigned)c.P) * c.Np + k);
-      });
+      for (unsigned j = (unsigned)t.a0 + threadIdx.x; j < (unsigned)t.a1; j += blockDim.x)
+        rq_unpack_one(c, tab, out, j, [&](unsigned q) {
+          const unsigned k = fdiv(q, c.divP);
+          return __ldcg(U + (long long)(q - k * (unsigned)c.P) * c.Np + k);
+        });
     }
   }
 }
