@@ -345,8 +345,11 @@ int setup_twopass(Plan& p) {
       if ((Mc * A) % Nc != 0) continue;
       const int64_t R1 = Mc * A / Nc;
       if (mode == kLoadRealPacked && (R1 % 2) != 0) continue;
-      // pass 2 geometry: W column pairs per CTA
-      const int W = (B <= 512) ? 16 : (B <= 1024) ? 8 : 4;
+      // pass 2 geometry: W column pairs per CTA.  Output rows are written in runs of W bins
+      // (32 bytes at W = 4); more columns per CTA (longer runs) cost shared memory and so
+      // concurrency: measured on 8 x 2^22, alpha 16, W = 4 is best from B = 512 to 2048
+      // (B = 1024: 4.40 ms against 4.53 ms at W = 8), W = 2 and 1 lose (6.1, 7.8 ms at B = 2048)
+      const int W = (B <= 256) ? 16 : 4;
       const int ncol = (mode == kLoadRealPacked) ? 2 * W : W;
       const int64_t region = B + B / 16 + 2;
       const int bits2 = (ilog2(B) + 1) / 2;
