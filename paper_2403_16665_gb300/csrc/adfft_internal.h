@@ -40,6 +40,8 @@ struct FoldChoice {
                      // 2: no staging, residues exchanged by bulk push copies (fused_push.cuh)
   int grid = 0;      // clusters launched: 0 = as many as can be resident at once (each loops over
                      // signals), -1 = one per signal, > 0 = that many
+  int vsplit = 0;    // columns of the two-pass form only, > 1: residues split over that many
+                     // independent CTAs per column (no cluster), each writing its own bins
 };
 
 // Launch geometry of the chirp-z kernel.
@@ -122,6 +124,8 @@ struct Plan {
   int64_t tp_A = 0, tp_B = 0;
   int64_t tp_force_A = 0;             // two-pass split chosen by the autotuner (0: the default rule)
   FusedLaunch tp1{};
+  FusedLaunch tp1f{};      // pass 1 forward with the residues split over independent CTAs
+  bool tp1f_ok = false;    // (FP32 forward only; the adjoint and precision forms use tp1)
   TwoPassLaunch tp2{};
   void* d_tp_tw1 = nullptr;           // pass-1 W_R1 table
   void* d_tp_post = nullptr;          // pass-1 row twiddles W_Mc

@@ -107,7 +107,7 @@ cudaError_t fused_launch(const FusedLaunch& L, const void* in, void* out, cudaSt
   a.in = in;
   a.out = out;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(a.C, L.grid_y, 1);
+  cfg.gridDim = dim3(a.vsplit > 1 ? a.vsplit : a.C, L.grid_y, 1);
   cfg.blockDim = dim3(L.threads, 1, 1);
   cfg.dynamicSmemBytes = L.smem;
   cfg.stream = stream;

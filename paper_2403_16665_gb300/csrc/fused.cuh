@@ -77,6 +77,9 @@ struct FusedArgs {
   // packed real input only: 1 = write the half spectrum X_0 .. X_{M/2} ([batch][M/2 + 1]
   // output), which determines the rest by X_{M-m} = conj X_m
   int half;
+  // kColumns only, > 1: that many CTAs per signal without a cluster (C = 1), CTA x holding
+  // residues [x RPC, (x + 1) RPC) and writing its own bins m = k P + r (runs of RPC bins)
+  int vsplit;
 };
 
 // Compile-time shape of a specialised instantiation; a zero field is read from
@@ -401,7 +404,9 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   TwTable<V> tab{tw_s, tw_s + a.tw_lo_n, a.tw_bits, (1u << a.tw_bits) - 1u};
 
   cg::cluster_group cluster = cg::this_cluster();
-  const int c = (int)blockIdx.x;          // rank within the cluster (grid.x == C)
+  const int c = (int)blockIdx.x;          // rank within the cluster (grid.x == C), or residue group
+  // (columns split over independent CTAs: each CTA's epilogue covers only its own residues)
+  const bool vs = MODE == kColumns && a.vsplit > 1;
 
   // Epilogue work split: CTA c writes bins j in [c*per, (c+1)*per) (real packed
   // input: j <= Mc/2 and their mirrors), per a multiple of P.  Thread t keeps the
@@ -409,17 +414,18 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   // take part), so its shared-memory sources are fixed for the whole kernel.
   const unsigned P = (unsigned)SH::p(a);
   const unsigned RPCu = (unsigned)SH::rpc(a);
-  const unsigned Tp = ((unsigned)SH::threads() / P) * P;
+  const unsigned EP = vs ? RPCu : P;                          // residues the epilogue covers
+  const unsigned Tp = ((unsigned)SH::threads() / EP) * EP;
   const bool lane_ok = threadIdx.x < Tp;
-  const unsigned r_l = threadIdx.x % P;
-  const unsigned k_step = Tp / P;
+  const unsigned r_l = vs ? c * RPCu + threadIdx.x % EP : threadIdx.x % P;
+  const unsigned k_step = Tp / EP;
   const unsigned jtot = (MODE == kLoadRealPacked) ? (unsigned)a.Mc / 2 + 1 : (unsigned)a.Mc;
   // (pair epilogue: per a multiple of 2P, so every CTA's k range starts even)
   constexpr unsigned KG = (SH::pairs && MODE == kLoadRealPacked && sizeof(V) == 8) ? 2u : 1u;
-  const unsigned per = ((jtot + a.C - 1) / a.C + KG * P - 1) / (KG * P) * (KG * P);
-  const unsigned j_first = c * per;
+  const unsigned per = vs ? jtot : ((jtot + a.C - 1) / a.C + KG * P - 1) / (KG * P) * (KG * P);
+  const unsigned j_first = vs ? 0u : c * per;
   const unsigned j_last = min(jtot, j_first + per) - 1;      // inclusive
-  const unsigned k_first = j_first / P + threadIdx.x / P;
+  const unsigned k_first = j_first / P + threadIdx.x / EP;
   // shared::cluster addresses of this lane's two source residue regions
   uint32_t base_u, base_p;
   {
@@ -427,8 +433,8 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
     const unsigned ou = r_l / RPCu, op = rp / RPCu;
     const V* lu = buf + (r_l - ou * RPCu) * SH::region(a);
     const V* lp = buf + (rp - op * RPCu) * SH::region(a);
-    base_u = dsmem_addr(lu, (a.C > 1) ? ou : (uint32_t)c);
-    base_p = dsmem_addr(lp, (a.C > 1) ? op : (uint32_t)c);
+    base_u = dsmem_addr(lu, (a.C > 1) ? ou : 0u);
+    base_p = dsmem_addr(lp, (a.C > 1) ? op : 0u);
   }
   const int r0 = c * SH::rpc(a);
   const Rl S = (Rl)a.scale;

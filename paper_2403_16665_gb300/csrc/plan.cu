@@ -117,6 +117,11 @@ int upload(void** dst, const std::vector<T>& v);
 // the cluster size (0: the smallest that fits) and whether staging may be
 // used.  Allocates the twiddle table in *d_tw unless one is passed in.
 // Returns ADFFT_OK or why the shape does not fit.
+// Two-pass forward, FP32: pass 1 with each column's residues over independent CTAs of this
+// many residues (runs of that many bins, 32 bytes at 4), instead of one CTA or cluster per column.
+constexpr bool kTwoPassSplitForward = true;
+constexpr int kTwoPassSplitResidues = 4;
+
 int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int64_t batch,
                     int64_t stage_bytes, int max_cluster, double scale, int* status,
                     FusedLaunch& L, void** d_tw, const FoldChoice& choice = FoldChoice{}) {
@@ -137,6 +142,8 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   const bool push = choice.stage == 2;   // bulk push exchange: one residue per CTA, no staging
   const bool can_stage = choice.stage != 0 && !push && stage_bytes > 0 && (stage_bytes % 16) == 0 &&
                          stage_bytes <= (int64_t)kSmemLimit;
+  const int vs = choice.vsplit > 1 ? choice.vsplit : 0;   // independent CTAs per column
+  if (vs && (mode != kColumns || push || P % vs)) return ADFFT_ERR_UNSUPPORTED_SIZE;
   int C = -1, stage = 0;
   size_t smem = 0;
   for (int pass = 0; pass < 2 && C < 0; ++pass) {
@@ -147,7 +154,8 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
       if (P % c) continue;
       if (choice.cluster > 0 && c != choice.cluster) continue;
       if (push && c != P) continue;
-      const int64_t rpc = P / c;
+      if (vs && c != 1) continue;
+      const int64_t rpc = vs ? P / vs : P / c;
       if (rpc * Np > max_vals) continue;
       const FusedSmem lay = fused_smem_layout(tw_n, st, (int)rpc, (int)region, (int)esz);
       if ((size_t)lay.total > kSmemLimit) continue;
@@ -158,7 +166,7 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
     }
   }
   if (C < 0) return ADFFT_ERR_UNSUPPORTED_SIZE;
-  const int64_t RPC = P / C;
+  const int64_t RPC = vs ? P / vs : P / C;
 
   FusedArgs& a = L.args;
   memset(&a, 0, sizeof(a));
@@ -180,6 +188,7 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   a.stage_bytes = stage;
   a.status = status;
   a.cols = 1;
+  a.vsplit = vs;
   a.in_unit = (mode == kLoadComplex || mode == kColumns) ? (int)esz : (int)(esz / 2);
   // passes: a first pass of radix R0 = 2^(log2 Np mod 4) (16 if that is 0), then radix 16;
   // for complex64 data a remainder of 2 is merged with one radix-16 pass into radix 32
@@ -220,8 +229,8 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
   a.tw = *d_tw;
 
   int threads = (int)((RPC * Np + vpt - 1) / vpt);
-  // the epilogue gives every residue at least one thread of each CTA
-  threads = (int)std::max<int64_t>(threads, P);
+  // the epilogue gives every residue it covers at least one thread of each CTA
+  threads = (int)std::max<int64_t>(threads, vs ? RPC : P);
   threads = std::max(32, (threads + 31) / 32 * 32);
   if (threads > kMaxThreads) return ADFFT_ERR_UNSUPPORTED_SIZE;
   L.mode = mode;
@@ -248,7 +257,8 @@ int configure_fused(bool dbl, int mode, int64_t Nc, int64_t Mc, int64_t Mt, int6
     cudaGetLastError();
     return cuda_status(e);
   }
-  const int resident = fused_max_active_clusters(L);
+  int resident = fused_max_active_clusters(L);
+  if (vs && resident > 0) resident = std::max(1, resident / vs);   // columns in flight
   if (C > 1 && resident < 1) return ADFFT_ERR_UNSUPPORTED_SIZE;
   // persistent grid: clusters loop over signals, so the table load and launch are paid once
   // per cluster and the next signal's input is fetched while the current one is transformed
@@ -322,10 +332,17 @@ int setup_fold(Plan& p, const FoldChoice* forced) {
   return ADFFT_OK;
 }
 
+bool split_forward_ok(const Plan& p, int64_t P1) {
+  return kTwoPassSplitForward && !p.dbl && P1 > kTwoPassSplitResidues && P1 % kTwoPassSplitResidues == 0;
+}
+
 // Configure the two-pass (four-step) path for power-of-two Nc: Nc = A B, pass 1 the
 // alpha-DFTs of the B columns of length A, pass 2 the B-point FFTs.  Without a forced A
-// (p.tp_force_A == 0) the longest A whose pass-1 transform fits one CTA (each CTA then
-// reads its strided column once), else clusters of at most 4, then 8 CTAs.
+// (p.tp_force_A == 0): where the FP32 forward can split pass 1 over independent CTAs, the
+// longest A with B >= 512 whose pass 1 fits a cluster of at most 4 CTAs (for the adjoint);
+// else the longest A whose pass-1 transform fits one CTA (each CTA then reads its strided
+// column once), else clusters of at most 4, then 8 CTAs.  (8 x 2^22, alpha 16: A = 4096,
+// forward 3.93 ms, against 4.60 ms at A = 1024.)
 int setup_twopass(Plan& p) {
   int mode;
   int64_t Nc, Mc;
@@ -335,16 +352,30 @@ int setup_twopass(Plan& p) {
   const size_t esz = p.dbl ? 16 : 8;
   const int vpt = fused_values_per_thread(p.dbl);
   const bool forced = p.tp_force_A > 0;
-  for (int max_c : {1, 4, 8, 16}) {
-    if (!forced && max_c == 16) break;
-    if (forced && max_c == 1) continue;
+  // rounds of (largest cluster for pass 1, smallest B, pass 1 must split for the forward)
+  struct Round {
+    int max_c;
+    int64_t min_B;
+    bool split;
+  };
+  static const Round kDefault[] = {{4, 512, true}, {1, 0, false}, {4, 0, false}, {8, 0, false}};
+  static const Round kForced[] = {{4, 0, false}, {8, 0, false}, {16, 0, false}};
+  const Round* rounds = forced ? kForced : kDefault;
+  const int nrounds = forced ? 3 : 4;
+  for (int ri = 0; ri < nrounds; ++ri) {
+    const int max_c = rounds[ri].max_c;
     for (int64_t A = Nc / 2; A >= 16; A >>= 1) {
       const int64_t B = Nc / A;
       if (B > 2048) break;
+      if (B < rounds[ri].min_B) continue;
       if (forced && A != p.tp_force_A) continue;
       if ((Mc * A) % Nc != 0) continue;
       const int64_t R1 = Mc * A / Nc;
       if (mode == kLoadRealPacked && (R1 % 2) != 0) continue;
+      if (rounds[ri].split) {
+        const int64_t g1 = gcd64(R1, A);
+        if (!split_forward_ok(p, R1 / (g1 & -g1))) continue;
+      }
       // pass 2 geometry: W column pairs per CTA.  Output rows are written in runs of W bins
       // (32 bytes at W = 4); more columns per CTA (longer runs) cost shared memory and so
       // concurrency: measured on 8 x 2^22, alpha 16, W = 4 is best from B = 512 to 2048
@@ -384,6 +415,32 @@ int setup_twopass(Plan& p) {
       L1.args.post_bits = pbits;
       L1.args.post_lo_n = lo_n;
       p.tp1 = L1;
+      // FP32 forward: the column's residues over independent CTAs of kTwoPassSplitResidues
+      // residues each (no cluster exchange; every CTA writes runs of that many bins)
+      p.tp1f_ok = false;
+      const int64_t P1 = L1.args.P;
+      if (split_forward_ok(p, L1.args.P)) {
+        FusedLaunch F{};
+        FoldChoice fc{};
+        fc.np = L1.args.Np;
+        fc.vsplit = (int)(P1 / kTwoPassSplitResidues);
+        const int rcf = configure_fused(p.dbl, kColumns, A, R1, R1, p.batch * B, A * (int64_t)esz, 1, 1.0,
+                                        p.d_status, F, &tw1, fc);
+        if (rcf == ADFFT_OK) {
+          const FusedArgs& s1 = L1.args;
+          F.args.cols = s1.cols;
+          F.args.in_stride = s1.in_stride;
+          F.args.M = s1.M;
+          F.args.Mpost = s1.Mpost;
+          F.args.post_tw = s1.post_tw;
+          F.args.post_bits = s1.post_bits;
+          F.args.post_lo_n = s1.post_lo_n;
+          p.tp1f = F;
+          p.tp1f_ok = true;
+        } else if (rcf != ADFFT_ERR_UNSUPPORTED_SIZE) {
+          return rcf;
+        }
+      }
       // pass 2 tables: W_B (shared memory), W_M (global, real unpacking)
       TwoPassLaunch& L2 = p.tp2;
       TwoPassArgs& t = L2.args;
@@ -454,6 +511,7 @@ int setup_twopass(Plan& p) {
         }
       }
       p.tp1.args.offs = p.d_offs;
+      p.tp1f.args.offs = p.d_offs;
       t.f.offs = p.d_offs;
       p.tp_A = A;
       p.tp_B = B;
@@ -472,6 +530,7 @@ void release_twopass(Plan& p) {
   }
   p.ws_bytes = 0;
   p.tp_ok = false;
+  p.tp1f_ok = false;
   p.tp_A = p.tp_B = 0;
 }
 
@@ -746,7 +805,7 @@ int launch_forward(Plan& p, const void* in, void* out, cudaStream_t s) {
     e = !tc ? fused_launch(p.fused, in, out, s)
             : f16 ? tc_launch_fused_fp16(p.fused, in, out, s) : tc_launch_fused_bf16(p.fused, in, out, s);
   } else if (p.tp_ok) {
-    e = !tc ? fused_launch(p.tp1, in, p.d_ws, s)
+    e = !tc ? fused_launch(p.tp1f_ok ? p.tp1f : p.tp1, in, p.d_ws, s)
             : f16 ? tc_launch_fused_fp16(p.tp1, in, p.d_ws, s) : tc_launch_fused_bf16(p.tp1, in, p.d_ws, s);
     if (e == cudaSuccess)
       e = !tc ? twopass_launch(p.tp2, p.d_ws, out, s)

@@ -30,6 +30,7 @@ void set_offsets(Plan& sub, const long long* d_offs) {
   sub.fused.args.offs = d_offs;
   sub.blu.args.f.offs = d_offs;
   sub.tp1.args.offs = d_offs;
+  sub.tp1f.args.offs = d_offs;
   sub.tp2.args.f.offs = d_offs;
 }
 
