@@ -28,10 +28,12 @@ KernelFn pick_r0(int r0) {
 // real fp32, packed sub-FFT 8192, 8 residues, 2 per CTA, 512 threads; padding of 2 slots per 32
 // elements (16-byte pairs stay aligned; the radix-32 first pass stores pairs without bank
 // conflicts in every quarter-warp), epilogue in pairs of k with 5 pair loads in flight per thread
-using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2, 5, 5, 2>;
+// (full-spectrum output; the half-spectrum variant below)
+using ShapeR32N8192P8 = Shape<13, 2, 8, 512, 2, 5, 5, 2, 1>;
+using ShapeR32N8192P8Half = Shape<13, 2, 8, 512, 2, 5, 5, 2, 2>;
 
 // the same with one residue per CTA (clusters of 8, 256 threads: two CTAs per SM)
-using ShapeR32N8192P8C8 = Shape<13, 1, 8, 256, 2, 5, 4, 2>;
+using ShapeR32N8192P8C8 = Shape<13, 1, 8, 256, 2, 5, 4, 2, 1>;
 
 bool is_r32_n8192_p8(const FusedLaunch& L, int rpc, int threads) {
   const FusedArgs& a = L.args;
@@ -41,9 +43,11 @@ bool is_r32_n8192_p8(const FusedLaunch& L, int rpc, int threads) {
 
 KernelFn pick_kernel(const FusedLaunch& L) {
   if (L.push) return push_forward(L);
-  if (is_r32_n8192_p8(L, 2, 512)) return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8>;
+  if (is_r32_n8192_p8(L, 2, 512))
+    return L.args.half ? fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8Half>
+                       : fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8>;
   if (KernelFn k = spec16k_forward(L)) return k;
-  if (is_r32_n8192_p8(L, 1, 256))
+  if (is_r32_n8192_p8(L, 1, 256) && !L.args.half)
     return fused_forward_kernel<float2, kLoadRealPacked, kVptF32, 32, 0, ShapeR32N8192P8C8>;
   if (L.dbl) {
     switch (L.mode) {

@@ -90,13 +90,17 @@ struct FusedArgs {
 // i.e. pad16).  With PW = 2 every even element index stays 16-byte aligned, and
 // float2 data moves in 16-byte pairs (first-pass stores, epilogue loads).
 // EU: independent epilogue loads in flight per thread (0: the generic default).
-template <int LOGNP = 0, int RPC = 0, int P = 0, int T = 0, int MTF = 0, int PADSH = 0, int EU = 0, int PW = 1>
+// HF: output extent of packed real input, 0: read at run time (FusedArgs::half), 1: the full
+// spectrum, 2: the half spectrum (fixed at compile time, the epilogue stores carry no test).
+template <int LOGNP = 0, int RPC = 0, int P = 0, int T = 0, int MTF = 0, int PADSH = 0, int EU = 0, int PW = 1,
+          int HF = 0>
 struct Shape {
   static constexpr bool fixed = LOGNP != 0 && RPC != 0 && P != 0 && T != 0 && MTF != 0;
   static constexpr int padsh = PADSH ? PADSH : 4;
   static constexpr int pw = PW;
   static constexpr bool pairs = PW == 2;
   static constexpr int eu = EU;
+  __device__ static __forceinline__ bool half(const struct FusedArgs& a);
   __device__ static __forceinline__ int pad(int p) { return p + PW * (p >> padsh); }
   __device__ static __forceinline__ int logNp(const struct FusedArgs& a);
   __device__ static __forceinline__ int Np(const struct FusedArgs& a);
@@ -106,8 +110,10 @@ struct Shape {
   __device__ static __forceinline__ int region(const struct FusedArgs& a);
   __device__ static __forceinline__ unsigned mt(const struct FusedArgs& a);
 };
-#define ADFFT_SHAPE_TPL template <int L, int R, int PP, int TT, int F, int PS, int E, int W>
-#define ADFFT_SHAPE Shape<L, R, PP, TT, F, PS, E, W>
+#define ADFFT_SHAPE_TPL template <int L, int R, int PP, int TT, int F, int PS, int E, int W, int H>
+#define ADFFT_SHAPE Shape<L, R, PP, TT, F, PS, E, W, H>
+ADFFT_SHAPE_TPL
+__device__ __forceinline__ bool ADFFT_SHAPE::half(const FusedArgs& a) { return H ? H == 2 : a.half != 0; }
 ADFFT_SHAPE_TPL
 __device__ __forceinline__ int ADFFT_SHAPE::logNp(const FusedArgs& a) { return L ? L : a.logNp; }
 ADFFT_SHAPE_TPL
@@ -130,7 +136,7 @@ using RuntimeShape = Shape<>;
 
 // Passes of a fixed shape: one of radix 2^LOGR0, then radix 16.
 template <class SH, int LOGR0> struct SH_PASSES;
-template <int L, int R, int PP, int TT, int F, int PS, int E, int W, int LOGR0>
+template <int L, int R, int PP, int TT, int F, int PS, int E, int W, int H, int LOGR0>
 struct SH_PASSES<ADFFT_SHAPE, LOGR0> { static constexpr int value = 1 + (L - LOGR0) / 4; };
 #undef ADFFT_SHAPE
 #undef ADFFT_SHAPE_TPL
@@ -438,6 +444,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
   }
   const int r0 = c * SH::rpc(a);
   const Rl S = (Rl)a.scale;
+  const bool half_out = SH::half(a);
   constexpr int LOGR0 = R0 == 1 ? 0 : R0 == 2 ? 1 : R0 == 4 ? 2 : R0 == 8 ? 3 : R0 == 16 ? 4 : 5;
   constexpr int kEpilogueUnroll = SH::eu ? SH::eu : epilogue_unroll<V, MODE>();
   uint32_t phase = 0, fail_phase = 0;
@@ -454,17 +461,10 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 
   for (long long sig = blockIdx.y; sig < a.batch; sig += gridDim.y) {
     const void* u;
+    bool ok = true;   // this thread saw the signal's input land
     if (staged) {
       u = stage;
-      // the CTA decides as one: after a wait ran out it transforms no further signal (it keeps
-      // taking part in the cluster barriers, so its peers are not left waiting)
-      const bool ok = failed || mbar_wait_bounded(bar, phase, wait_limit);
-      if (__syncthreads_or(!ok) && !failed) {
-        failed = true;
-        fail_phase = phase;
-        if (threadIdx.x == 0 && a.status) atomicExch(a.status, kStatusTimeout);
-      }
-      phase ^= 1u;
+      if (!failed) ok = mbar_wait_bounded(bar, phase, wait_limit);
     } else if (MODE == kColumns) {
       u = reinterpret_cast<const V*>(reinterpret_cast<const unsigned char*>(a.in) + sig_in_bytes(a, sig / a.cols)) +
           (sig % a.cols);
@@ -491,11 +491,23 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
 
     // ---- K1: fold + residue twiddle + first radix
     if (a.C > 1 && sig != (long long)blockIdx.y) cluster_wait();
-    if (!failed) {
+    if (!failed && ok) {
       if (staged || col_staged) first_pass<R0, V, true, SH>(a, u, reinterpret_cast<const V*>(stage), MODE, buf, tab, r0);
       else first_pass<R0, V, false, SH>(a, u, nullptr, MODE, buf, tab, r0);
     }
-    __syncthreads();
+    if (staged) {
+      // the CTA decides as one, on the barrier that ends the first pass: after a wait ran out
+      // it transforms no further signal (it keeps taking part in the cluster barriers, so its
+      // peers are not left waiting); the first pass has no barrier of its own
+      if (__syncthreads_or(!ok) && !failed) {
+        failed = true;
+        fail_phase = phase;
+        if (threadIdx.x == 0 && a.status) atomicExch(a.status, kStatusTimeout);
+      }
+      phase ^= 1u;
+    } else {
+      __syncthreads();
+    }
 
     // prefetch the next signal's input while this one is transformed
     const long long nxt = sig + gridDim.y;
@@ -578,7 +590,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
               X2[h] = csub(hA, t);
               if (j <= lim) {
                 st_stream(out + j, X1[h]);
-                if (!a.half || j == 0) st_stream(out + j + Mc, X2[h]);
+                if (!half_out || j == 0) st_stream(out + j + Mc, X2[h]);
               }
             }
             // mirror bins: lanes of residue 0 store their two values in the opposite order, so
@@ -591,7 +603,7 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
               const unsigned j = (k + (sw ? 1 - h : h)) * P + r_l;
               if (j <= lim && j != 0 && 2 * j != Mc) {
                 st_stream(out + (Mc - j), cconj(y2));
-                if (!a.half) st_stream(out + ((unsigned long long)a.M - j), cconj(y1));
+                if (!half_out) st_stream(out + ((unsigned long long)a.M - j), cconj(y1));
               }
             }
           }
@@ -623,10 +635,10 @@ __global__ void __launch_bounds__(512) fused_forward_kernel(const FusedArgs a) {
               const V X1 = cscale(cadd(E, wO), S);
               const V X2 = cscale(csub(E, wO), S);
               st_stream(out + j, X1);
-              if (!a.half || j == 0) st_stream(out + j + Mc, X2);
+              if (!half_out || j == 0) st_stream(out + j + Mc, X2);
               if (j != 0 && 2 * j != Mc) {
                 st_stream(out + (Mc - j), cconj(X2));
-                if (!a.half) st_stream(out + ((unsigned long long)a.M - j), cconj(X1));
+                if (!half_out) st_stream(out + ((unsigned long long)a.M - j), cconj(X1));
               }
             }
           }

@@ -322,6 +322,15 @@ int setup_fold(Plan& p, const FoldChoice* forced) {
   p.fused.args.M = p.M;
   p.fused.args.offs = p.d_offs;
   p.fused.args.half = p.half ? 1 : 0;
+  if (p.half) {
+    // half-spectrum output has kernels of its own: set their launch attributes too
+    cudaError_t e = fused_prepare(p.fused);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p.fold_ok = false;
+      return cuda_status(e);
+    }
+  }
   if (p.fault.copy_skip >= 0) {
     p.fused.args.fault_sig1 = p.fault.copy_skip + 1;
     p.fused.args.wait_limit = 20000000;   // ~10 ms of SM clock

@@ -11,7 +11,10 @@ namespace adfft {
 namespace {
 
 template <int P>
-using Shape16k = Shape<14, 1, P, 512, 2, 5, 5, 2>;
+using Shape16k = Shape<14, 1, P, 512, 2, 5, 5, 2, 1>;   // full-spectrum output
+
+template <int P>
+using Shape16kHalf = Shape<14, 1, P, 512, 2, 5, 5, 2, 2>;   // half-spectrum output
 
 template <int P>
 using AdjShape16k = Shape<14, 1, P, 512, 2, 5, 0, 2>;
@@ -26,6 +29,17 @@ bool is_16k(const FusedLaunch& L) {
 
 SpecKernel spec16k_forward(const FusedLaunch& L) {
   if (!is_16k(L)) return nullptr;
+  if (L.args.half) {
+    switch (L.args.P) {
+      case 3: return fused_forward_kernel<float2, kLoadRealPacked, 32, 4, 0, Shape16kHalf<3>>;
+      case 4: return fused_forward_kernel<float2, kLoadRealPacked, 32, 4, 0, Shape16kHalf<4>>;
+      case 5: return fused_forward_kernel<float2, kLoadRealPacked, 32, 4, 0, Shape16kHalf<5>>;
+      case 6: return fused_forward_kernel<float2, kLoadRealPacked, 32, 4, 0, Shape16kHalf<6>>;
+      case 8: return fused_forward_kernel<float2, kLoadRealPacked, 32, 4, 0, Shape16kHalf<8>>;
+      case 16: return fused_forward_kernel<float2, kLoadRealPacked, 32, 4, 0, Shape16kHalf<16>>;
+      default: return nullptr;
+    }
+  }
   switch (L.args.P) {
     case 3: return fused_forward_kernel<float2, kLoadRealPacked, 32, 4, 0, Shape16k<3>>;
     case 4: return fused_forward_kernel<float2, kLoadRealPacked, 32, 4, 0, Shape16k<4>>;
