@@ -2,6 +2,7 @@
 
     python -m paper_2403_16665_gb300.profile --workload batch_r32 --batch 256 --iters 4
     python -m paper_2403_16665_gb300.profile --workload ragged_r32 --batch 10000 --iters 10
+    python -m paper_2403_16665_gb300.profile --workload ragged_r32 --batch 10000 --iters 10 --subsets
     python -m paper_2403_16665_gb300.profile --probes [write|dsmem|overlap|l2|place]
 
 Inputs come from the seeded generators in signals.py; every iteration is one
@@ -36,6 +37,8 @@ def main():
     ap.add_argument("--shape", default=None,
                     help="fold launch shape fft_len,cluster,staged[,grid] (adfft_plan_set_launch_shape)")
     ap.add_argument("--half", action="store_true", help="half-spectrum output (real input: bins 0 .. M/2)")
+    ap.add_argument("--subsets", action="store_true",
+                    help="ragged_r32: class graph against the queue form on subsets of the mix")
     ap.add_argument("--probes", nargs="?", const="all", default=None,
                     help="build and run the exchange-path micro-benchmarks (write, dsmem, overlap, l2, "
                          "place or all) instead of a workload")
@@ -44,7 +47,7 @@ def main():
         return probes(args.probes)
     _build.build()
     if args.workload == "ragged_r32":
-        return ragged(args)
+        return ragged_subsets(args) if args.subsets else ragged(args)
     gen = getattr(signals, args.workload)
     kw = dict(batch=args.batch)
     if args.N:
@@ -119,6 +122,35 @@ def _time(fn, iters):
     e1.record(s)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / max(1, iters)
+
+
+def ragged_subsets(args):
+    """Forward of the class graph and of the queue form on subsets of the ragged mix (a ragged
+    plan built from each subset's signals, random input)."""
+    import torch
+
+    from paper_2403_16665_gb300 import adfft, signals
+
+    Ns, alphas = signals.ragged_shapes(args.batch)
+    Ms = np.rint(Ns * alphas).astype(np.int64)
+    dev = torch.device("cuda:0")
+    subsets = [("all", np.ones(len(Ns), bool)), ("M > 32768", Ms > 32768), ("M <= 32768", Ms <= 32768),
+               ("N = 65536, M = 524288", (Ns == 65536) & (Ms == 524288)), ("N = 16384", Ns == 16384),
+               ("N <= 2048", Ns <= 2048)]
+    for name, sel in subsets:
+        plan = adfft.RaggedPlan(Ns[sel], alphas[sel], adfft.R32)
+        x = torch.randn(int(plan.in_off[-1]), device=dev)
+        X = torch.empty(int(plan.out_off[-1]), dtype=torch.complex64, device=dev)
+        nbytes = x.numel() * 4 + X.numel() * 8
+        plan.set_form(adfft.RAGGED_CLASSES)
+        tg = _time(lambda: plan.execute(x.data_ptr(), X.data_ptr()), args.iters)
+        try:
+            plan.set_form(adfft.RAGGED_QUEUE)
+            tq = _time(lambda: plan.execute(x.data_ptr(), X.data_ptr()), args.iters)
+        except adfft.AdfftError:
+            tq = float("nan")
+        print("ragged subset %-24s signals %5d  %.3f GB  class graph %.4f ms (%.0f GB/s)  queue %.4f ms (%.0f GB/s)"
+              % (name, int(sel.sum()), nbytes / 1e9, tg, nbytes / tg / 1e6, tq, nbytes / tq / 1e6))
 
 
 def ragged(args):
