@@ -387,9 +387,11 @@ int setup_twopass(Plan& p) {
       }
       // pass 2 geometry: W column pairs per CTA.  Output rows are written in runs of W bins
       // (32 bytes at W = 4); more columns per CTA (longer runs) cost shared memory and so
-      // concurrency: measured on 8 x 2^22, alpha 16, W = 4 is best from B = 512 to 2048
-      // (B = 1024: 4.40 ms against 4.53 ms at W = 8), W = 2 and 1 lose (6.1, 7.8 ms at B = 2048)
-      const int W = (B <= 256) ? 16 : 4;
+      // concurrency: measured on 8 x 2^22, alpha 16, W = 4 is best for the forward from B = 1024
+      // to 2048 (B = 1024: 4.40 ms against 4.53 ms at W = 8), W = 2 and 1 lose (6.1, 7.8 ms at
+      // B = 2048); at B = 512 W = 4 and 8 tie for the forward and W = 8 is 0.3 ms faster for
+      // the adjoint (7.09 against 7.41 ms), W = 16 slower for both
+      const int W = (B <= 256) ? 16 : (B <= 512) ? 8 : 4;
       const int ncol = (mode == kLoadRealPacked) ? 2 * W : W;
       const int64_t region = B + B / 16 + 2;
       const int bits2 = (ilog2(B) + 1) / 2;

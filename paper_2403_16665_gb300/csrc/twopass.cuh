@@ -26,7 +26,7 @@ struct TwoPassArgs {
   int B, logB;
   long long R1;         // row length alpha A
   long long Mc, M;
-  int W;                // column pairs per CTA (4 or 16: a power of two, as is B)
+  int W;                // column pairs per CTA (4, 8 or 16: a power of two, as is B)
   int real_packed;
   const void* wM;       // two-level W_M table (global memory), for the real unpacking
   int wM_bits, wM_lo_n;
