@@ -269,14 +269,18 @@ int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *s
  * 16 blocks (the fold identity holds for every divisor of the gcd), the
  * smallest such cluster, input staging where it fits, and as many clusters as
  * can be resident at once, each looping over signals; the two-pass form only
- * where no single-pass shape fits.
+ * where no single-pass shape fits, with the split g = A*B (FP32): the longest A
+ * with B >= 512 whose pass 1 fits 4 CTAs, the FP32 forward's pass 1 spreading
+ * each column's residues over independent CTAs of 4 residues.
  *
  * adfft_plan_autotune times the forward transform of the plan (flags 0) or the
  * forward transform and its adjoint (ADFFT_TUNE_WITH_ADJOINT) for every
  * candidate launch shape (sub-FFT length, cluster size, input staging, a
  * resident-size or one-per-signal grid; the two-pass form, with every split
  * of its transform length into A*B, where it applies) with `iters` timed launches each (1..100;
- * 0 means 3) on the caller's buffers, keeps the fastest, and records it in
+ * 0 means 3) on the caller's buffers, times the candidates within 5 % of the
+ * fastest (at most three) again in three alternating rounds, keeps the one with
+ * the smallest time, and records it in
  * the process-wide tuning cache under (GPU name, driver version, N, M, batch,
  * dtype, precision).  d_in and d_out are as for adfft_execute (d_out is
  * overwritten); for a ragged plan the packed buffers, and every shape class
