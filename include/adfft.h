@@ -269,9 +269,11 @@ int adfft_execute_host(adfft_plan_t plan, const void *h_in, void *h_out, void *s
  * 16 blocks (the fold identity holds for every divisor of the gcd), the
  * smallest such cluster, input staging where it fits, and as many clusters as
  * can be resident at once, each looping over signals; the two-pass form only
- * where no single-pass shape fits, with the split g = A*B (FP32): the longest A
- * with B >= 512 whose pass 1 fits 4 CTAs, the FP32 forward's pass 1 spreading
- * each column's residues over independent CTAs of 4 residues.
+ * where no single-pass shape fits.  Its split g = A*B: for FP32 plans whose pass 1
+ * has a residue count that is a multiple of 4 above 4, the longest A with B >= 512
+ * whose pass 1 fits 4 CTAs (the forward's pass 1 then spreads each column's residues
+ * over independent CTAs of 4 residues); otherwise the longest A whose pass 1 fits
+ * one CTA, else clusters of up to 4, then 8.
  *
  * adfft_plan_autotune times the forward transform of the plan (flags 0) or the
  * forward transform and its adjoint (ADFFT_TUNE_WITH_ADJOINT) for every
