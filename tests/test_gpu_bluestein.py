@@ -46,7 +46,14 @@ def test_chirp_z_sizes(dtype_code, N, M):
     torch = _torch()
     dbl = dtype_code in (adfft.R64, adfft.C128)
     if dbl and 2 * N > 8192:
-        pytest.skip("beyond the fp64 chirp-z length (2N <= 8192)")
+        # the FP64 chirp-z kernel holds a padded length of at most 8192 in one CTA; a refusal
+        # of the forced algorithm is that stated limit
+        try:
+            adfft.Plan(N, batch=1, dtype=dtype_code, M=M).set_algorithm(adfft.ALGO_BLUESTEIN)
+        except adfft.AdfftError as e:
+            if e.code not in (-3, -9):
+                raise
+            pytest.skip("fp64 chirp-z beyond a padded length of 8192 (2N - 1 > 8192): %s" % e)
     rng = np.random.default_rng(N * 13 + M)
     x = rng.standard_normal((2, N))
     if dtype_code in (adfft.C64, adfft.C128):
