@@ -8,7 +8,8 @@ cost argument of Sec. 4, Eq. 16), cuFFT on the input zero-padded to M points
 through torch.fft, with the padding included in its time.  cuFFT runs here
 only; the library never calls it.  Accuracy against the FP64 oracle is given
 on sampled bins for every form timed (cuFFT's output scaled by S = 1/N, the
-library's default scale).
+library's default scale).  The ragged batch is timed as the class graph (forward, adjoint)
+and as one persistent work-queue kernel (forward), with the two forwards' difference.
 """
 from __future__ import annotations
 
@@ -196,6 +197,19 @@ def context(dev, iters=5, seed_bins=11):
         d = {"forward": _entry(ms, X.numel(), nbytes)}
         ms = _time(lambda: plan.execute_adjoint(X.data_ptr(), xb.data_ptr()), iters)
         d["adjoint"] = _entry(ms, X.numel(), nbytes)
+        try:
+            # the same forward as one persistent work-queue kernel, against the class graph
+            Xq = torch.empty_like(X)
+            plan.set_form(adfft.RAGGED_QUEUE)
+            ms = _time(lambda: plan.execute(x.data_ptr(), Xq.data_ptr()), iters)
+            plan.set_form(adfft.RAGGED_CLASSES)
+            plan.execute(x.data_ptr(), X.data_ptr())
+            torch.cuda.synchronize()
+            rel = (torch.linalg.vector_norm(Xq - X) / torch.linalg.vector_norm(X)).item()
+            d["queue_forward"] = _entry(ms, X.numel(), nbytes, rel_diff_vs_class_graph=rel)
+            del Xq
+        except Exception as e:
+            d["queue_forward"] = {"error": repr(e)[:200]}
         res["ragged_r32_10000"] = d
         del x, X, xb
         torch.cuda.empty_cache()
