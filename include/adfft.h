@@ -180,6 +180,27 @@ typedef enum {
  */
 int adfft_plan_set_ragged_form(adfft_plan_t plan, int form);
 
+/*
+ * Inspection of the queue form: the tile list that ADFFT_RAGGED_QUEUE runs for a ragged batch
+ * of these shapes (N[i], alpha[i], as for adfft_plan_create_ragged), computed on the host from
+ * the shapes alone (no device, no CUDA call).  Shape classes are the distinct (N, M) in
+ * increasing order, as the ragged plan forms them.  lag: fft tiles between a split signal's
+ * last fft tile and its first unpack tile (a plan uses its resident CTA count, e.g. 608).
+ * Each tile is 5 int32 at tiles[5 i ..]: kind (0 whole, 1 fft, 2 unpack), class, then
+ *   whole:  index of its first signal in whole[], 0, number of signals;
+ *   fft:    signal, first residue, number of residues;
+ *   unpack: signal, first leader bin, end leader bin (exclusive).
+ * whole[] lists the signals of the whole tiles, tile after tile.  *ntiles and *nwhole receive
+ * the counts; with tiles / whole NULL only the counts are written.  ADFFT_ERR_INVALID_ARG for
+ * a capacity below the count, ADFFT_ERR_NOT_SUPPORTED for shapes the queue form cannot
+ * serve (the same condition as adfft_plan_set_ragged_form), ADFFT_ERR_INVALID_ALPHA as for
+ * plan creation.  The paper's method, generalised per signal (Sec. 3, Eqs. 10-13), is what
+ * the tiles compute; the layout itself is this library's scheduling.
+ */
+int adfft_ragged_queue_layout(const int64_t *N, const double *alpha, int64_t count, int dtype, int32_t lag,
+                              int32_t *tiles, int64_t tile_capacity, int64_t *ntiles, int64_t *whole,
+                              int64_t whole_capacity, int64_t *nwhole);
+
 /* Packed offsets of a ragged plan (arrays of count+1 entries; either may be NULL).
  * For a uniform plan: in_off[i] = i*N, out_off[i] = i*M. */
 int adfft_plan_offsets(adfft_plan_t plan, int64_t *in_off, int64_t *out_off);

@@ -42,7 +42,7 @@ EXPORTS = (
     "adfft_execute_adjoint", "adfft_execute_host", "adfft_plan_sync_status",
     "adfft_execute_noalloc", "adfft_plan_autotune", "adfft_autotune_save", "adfft_autotune_load",
     "adfft_autotune_clear", "adfft_plan_set_launch_shape", "adfft_plan_set_output",
-    "adfft_plan_set_ragged_form",
+    "adfft_plan_set_ragged_form", "adfft_ragged_queue_layout",
 )
 
 
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "adfft_autotune_load": ([ctypes.c_char_p], i32),
         "adfft_autotune_clear": ([], i32),
         "adfft_plan_set_launch_shape": ([vp, i64, i32, i32, i32], i32),
+        "adfft_ragged_queue_layout": ([vp, vp, i64, i32, i32, vp, i64, vp, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -247,6 +248,26 @@ def _ragged_set_form(self, form):
 
 
 RaggedPlan.set_form = _ragged_set_form
+
+
+def ragged_queue_layout(Ns, alphas, dtype=R32, lag=608):
+    """adfft_ragged_queue_layout: the queue form's tiles for these shapes, computed on the host
+    (no device needed).  Returns (tiles, whole): tiles an (n, 5) int32 array of (kind, class,
+    signal or first whole index, a0, a1), whole the signals of the whole tiles in order."""
+    import numpy as np
+    lib = load()
+    N = np.ascontiguousarray(np.asarray(Ns, dtype=np.int64))
+    A = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    nt, nw = ctypes.c_int64(0), ctypes.c_int64(0)
+    args = (N.ctypes.data_as(ctypes.c_void_p), A.ctypes.data_as(ctypes.c_void_p), int(N.size), int(dtype), int(lag))
+    _check(lib.adfft_ragged_queue_layout(*args, None, 0, ctypes.byref(nt), None, 0, ctypes.byref(nw)),
+           "adfft_ragged_queue_layout")
+    tiles = np.zeros((max(nt.value, 1), 5), dtype=np.int32)
+    whole = np.zeros(max(nw.value, 1), dtype=np.int64)
+    _check(lib.adfft_ragged_queue_layout(*args, tiles.ctypes.data_as(ctypes.c_void_p), nt.value, ctypes.byref(nt),
+                                         whole.ctypes.data_as(ctypes.c_void_p), nw.value, ctypes.byref(nw)),
+           "adfft_ragged_queue_layout")
+    return tiles[:nt.value], whole[:nw.value]
 
 
 def autotune_save(path):

@@ -218,6 +218,9 @@ int cuda_status_of(cudaError_t e);
 adfft_plan_s* ragged_create(const int64_t* N, const double* alpha, int64_t count, int dtype, int* err);
 int ragged_execute(Plan& p, const void* in, void* out, cudaStream_t s, int which);
 void ragged_release(Plan& p);
+int ragged_queue_layout(const int64_t* N, const double* alpha, int64_t count, int dtype, int lag,
+                        int32_t* tiles_out, int64_t tile_capacity, int64_t* ntiles, int64_t* whole_out,
+                        int64_t whole_capacity, int64_t* nwhole);
 int ragged_set_form(Plan& p, int form);              // ADFFT_RAGGED_CLASSES / ADFFT_RAGGED_QUEUE
 int ragged_queue_status(Plan& p, int* status);       // read and clear the queue kernel's status word
 

@@ -1077,6 +1077,13 @@ int adfft_plan_set_ragged_form(adfft_plan_t plan, int form) {
   return ragged_set_form(plan->p, form);
 }
 
+int adfft_ragged_queue_layout(const int64_t* N, const double* alpha, int64_t count, int dtype, int32_t lag,
+                              int32_t* tiles, int64_t tile_capacity, int64_t* ntiles, int64_t* whole,
+                              int64_t whole_capacity, int64_t* nwhole) {
+  return adfft::ragged_queue_layout(N, alpha, count, dtype, (int)lag, tiles, tile_capacity, ntiles, whole,
+                                    whole_capacity, nwhole);
+}
+
 int adfft_plan_set_output(adfft_plan_t plan, int mode) {
   using namespace adfft;
   if (!plan || (mode != ADFFT_OUTPUT_FULL && mode != ADFFT_OUTPUT_HALF)) return ADFFT_ERR_INVALID_ARG;

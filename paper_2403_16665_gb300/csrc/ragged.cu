@@ -146,6 +146,115 @@ int whole_group(const RqClass& k) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(kRqMaxGroup, kRqTilePoints / ((int64_t)k.P * k.Np)));
 }
 
+// ---- layout of the queue form on the host (no CUDA call: adfft_ragged_queue_layout uses it too)
+
+// Queue geometry of a shape class from its core shape (load mode, Nc input elements, Mc bins)
+// and its M output bins: packed real (even N and M) or complex input, the largest
+// power-of-two sub-FFT dividing gcd(Mc, Nc) that one tile holds, with a fold of at most 64.
+// ADFFT_ERR_UNSUPPORTED_SIZE where the queue form has no geometry for the class.
+int rq_geometry(int mode, int64_t Nc, int64_t Mc, int64_t M, RqClass& k) {
+  if (mode != kLoadRealPacked && mode != kLoadComplex) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  const int64_t gg = plan_gcd(Mc, Nc);
+  int64_t Np = gg & -gg;
+  while (Np > kRqTilePoints) Np /= 2;
+  if (Nc / Np > 64 || Mc >= (int64_t(1) << 30)) return ADFFT_ERR_UNSUPPORTED_SIZE;
+  memset(&k, 0, sizeof(k));
+  k.Np = (int)Np;
+  k.logNp = 0;
+  while ((1 << k.logNp) < k.Np) ++k.logNp;
+  k.P = (int)(Mc / Np);
+  k.q = (int)(Nc / Np);
+  k.Nc = (int)Nc;
+  k.Mc = (int)Mc;
+  k.Mt = (int)(mode == kLoadRealPacked ? M : Mc);
+  k.region = k.Np + k.Np / 16 + 2;
+  int lr0 = (k.logNp == 0) ? 0 : (k.logNp % 4 ? k.logNp % 4 : 4);
+  if (lr0 == 1 && k.logNp >= 5) lr0 = 5;   // radix 2 merged with one radix-16 pass into radix 32
+  k.nrad = 1 + (k.logNp - lr0) / 4;
+  k.r0 = 1 << lr0;
+  k.real_packed = mode == kLoadRealPacked ? 1 : 0;
+  k.M = M;
+  k.divP = make_fastdiv((uint32_t)k.P);
+  return ADFFT_OK;
+}
+
+bool rq_split(const RqClass& k) { return (int64_t)k.P * k.Np > kRqTilePoints; }
+
+struct RqLayout {
+  std::vector<RqTile> tiles;
+  std::vector<int> whole;           // signals of the whole tiles, tile after tile
+  std::vector<int> nfft;            // per signal: its fft tiles (0: a whole signal)
+  std::vector<long long> scratch;   // per signal: float2 offset of its U in the scratch area
+  long long scratch_total = 0;
+};
+
+// Tile order: split signals (residues beyond one tile) largest first, each signal's fft tiles
+// followed, at least `lag` tiles later (about one wave of resident CTAs, so that an unpack
+// tile seldom waits for fft tiles still running), by its unpack tiles; then the whole tiles of
+// each class, classes with the most work first.  An unpack tile waits only for fft tiles
+// earlier in the queue, which never wait: no cycle.
+void rq_layout(const std::vector<RqClass>& cls, const std::vector<std::vector<int64_t>>& members, int64_t count,
+               int lag, RqLayout& L) {
+  const size_t ncls = cls.size();
+  L.tiles.clear();
+  L.whole.clear();
+  L.nfft.assign((size_t)count, 0);
+  L.scratch.assign((size_t)count, 0);
+  L.scratch_total = 0;
+  std::vector<int> cls_of((size_t)count, -1);
+  for (size_t c = 0; c < ncls; ++c)
+    for (int64_t s : members[c]) cls_of[(size_t)s] = (int)c;
+  std::vector<std::pair<int64_t, int64_t>> split;   // (-M, signal)
+  for (int64_t s = 0; s < count; ++s) {
+    const RqClass& k = cls[(size_t)cls_of[(size_t)s]];
+    if (rq_split(k)) {
+      L.scratch[(size_t)s] = L.scratch_total;
+      L.scratch_total += (long long)k.P * k.Np;
+      const int rpt = std::min(k.P, kRqTilePoints / k.Np);
+      L.nfft[(size_t)s] = (k.P + rpt - 1) / rpt;
+      split.push_back({-k.M, s});
+    }
+  }
+  std::sort(split.begin(), split.end());
+  auto unpack_tiles = [&](int64_t s) {
+    const int c = cls_of[(size_t)s];
+    const RqClass& k = cls[(size_t)c];
+    const int jt = k.real_packed ? k.Mc / 2 + 1 : k.Mc;
+    for (int j0 = 0; j0 < jt; j0 += kRqLeadersPerTile)
+      L.tiles.push_back(RqTile{kRqUnpack, c, (int)s, j0, std::min(jt, j0 + kRqLeadersPerTile), 0});
+  };
+  std::vector<std::pair<size_t, int64_t>> pending;   // (tiles emitted after its fft tiles, signal)
+  size_t next = 0;
+  for (size_t i = 0; i < split.size(); ++i) {
+    const int64_t s = split[i].second;
+    const int c = cls_of[(size_t)s];
+    const RqClass& k = cls[(size_t)c];
+    const int rpt = std::min(k.P, kRqTilePoints / k.Np);
+    for (int r = 0; r < k.P; r += rpt) L.tiles.push_back(RqTile{kRqFft, c, (int)s, r, std::min(rpt, k.P - r), 0});
+    pending.push_back({L.tiles.size(), s});
+    while (next < pending.size() && pending[next].first + (size_t)lag <= L.tiles.size())
+      unpack_tiles(pending[next++].second);
+  }
+  while (next < pending.size()) unpack_tiles(pending[next++].second);
+  std::vector<std::pair<int64_t, size_t>> corder;
+  for (size_t c = 0; c < ncls; ++c) {
+    const RqClass& k = cls[c];
+    if (rq_split(k)) continue;
+    const int64_t n = k.real_packed ? 2 * (int64_t)k.Nc : (int64_t)k.Nc;
+    corder.push_back({-(int64_t)members[c].size() * (k.M + n), c});
+  }
+  std::sort(corder.begin(), corder.end());
+  for (auto& co : corder) {
+    const size_t c = co.second;
+    const int per = whole_group(cls[c]);
+    for (size_t i = 0; i < members[c].size(); i += per) {
+      const int cnt = (int)std::min<size_t>(per, members[c].size() - i);
+      L.tiles.push_back(RqTile{kRqWhole, (int)c, (int)L.whole.size(), 0, cnt, 0});
+      for (int w = 0; w < cnt; ++w) L.whole.push_back((int)members[c][i + w]);
+    }
+  }
+}
+
 // Build the tile queue of the persistent form from the shape classes' fold geometry.
 // Returns ADFFT_OK (p.rq_ok set), ADFFT_ERR_UNSUPPORTED_SIZE when a class has no
 // single-CTA fold geometry (then only the class graph serves the plan), or an error.
@@ -158,35 +267,13 @@ int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
   for (size_t c = 0; c < ncls; ++c) {
     const Plan& q = p.r_sub[c]->p;
     if (q.dbl) return ADFFT_ERR_UNSUPPORTED_SIZE;
-    // fold geometry of the class: packed real (even N and M) or complex input; the largest
-    // power-of-two sub-FFT dividing gcd(Mc, Nc) that one tile holds, with a fold of <= 64
     int mode;
     int64_t Nc, Mc;
     core_shape(q, &mode, &Nc, &Mc);
-    if (mode != kLoadRealPacked && mode != kLoadComplex) return ADFFT_ERR_UNSUPPORTED_SIZE;
-    const int64_t gg = plan_gcd(Mc, Nc);
-    int64_t Np = gg & -gg;
-    while (Np > kRqTilePoints) Np /= 2;
-    if (Nc / Np > 64 || Mc >= (int64_t(1) << 30)) return ADFFT_ERR_UNSUPPORTED_SIZE;
     RqClass& k = cls[c];
-    memset(&k, 0, sizeof(k));
-    k.Np = (int)Np;
-    k.logNp = 0;
-    while ((1 << k.logNp) < k.Np) ++k.logNp;
-    k.P = (int)(Mc / Np);
-    k.q = (int)(Nc / Np);
-    k.Nc = (int)Nc;
-    k.Mc = (int)Mc;
-    k.Mt = (int)(mode == kLoadRealPacked ? q.M : Mc);
-    k.region = k.Np + k.Np / 16 + 2;
-    int lr0 = (k.logNp == 0) ? 0 : (k.logNp % 4 ? k.logNp % 4 : 4);
-    if (lr0 == 1 && k.logNp >= 5) lr0 = 5;   // radix 2 merged with one radix-16 pass into radix 32
-    k.nrad = 1 + (k.logNp - lr0) / 4;
-    k.r0 = 1 << lr0;
-    k.real_packed = mode == kLoadRealPacked ? 1 : 0;
-    k.M = q.M;
+    const int rcg = rq_geometry(mode, Nc, Mc, q.M, k);
+    if (rcg != ADFFT_OK) return rcg;
     k.scale = (float)q.scale;
-    k.divP = make_fastdiv((uint32_t)k.P);
     int bits, lo_n, hi_n;
     std::vector<float> t = twiddle_table_f32(k.Mt, &bits, &lo_n, &hi_n);
     k.tw_bits = bits;
@@ -197,8 +284,7 @@ int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
     tw_max = std::max(tw_max, lo_n + hi_n);
     // regions a tile holds: R of the residues of a split signal, or the P residues of each
     // signal of a whole tile
-    const int rpt = (int64_t)k.P * k.Np > kRqTilePoints ? std::min(k.P, kRqTilePoints / k.Np)
-                                                        : whole_group(k) * k.P;
+    const int rpt = rq_split(k) ? std::min(k.P, kRqTilePoints / k.Np) : whole_group(k) * k.P;
     buf_max = std::max(buf_max, (size_t)rpt * (size_t)k.region * 8);
   }
   const size_t smem = (((size_t)tw_max * 8 + 15) & ~size_t(15)) + buf_max;
@@ -212,71 +298,20 @@ int build_queue(Plan& p, const std::vector<std::vector<int64_t>>& members) {
     return ADFFT_ERR_UNSUPPORTED_SIZE;
   }
   const int resident = per_sm * sms;
-  const int lag = resident;
 
-  // signals and tiles: split signals (residues beyond one tile) largest first, each signal's
-  // fft tiles followed by the unpack tiles of the split signal before it; then the whole
-  // tiles of each class, classes with the most work first
+  RqLayout lay;
+  rq_layout(cls, members, p.r_count, resident, lay);
+  const std::vector<RqTile>& tiles = lay.tiles;
+  const std::vector<int>& whole = lay.whole;
+  const long long scratch = lay.scratch_total;
   std::vector<RqSignal> sigs((size_t)p.r_count);
-  std::vector<RqTile> tiles;
-  std::vector<int> whole;
-  std::vector<std::pair<int64_t, int64_t>> split;   // (-M, signal)
-  std::vector<int> cls_of((size_t)p.r_count, -1);
-  for (size_t c = 0; c < ncls; ++c)
-    for (int64_t s : members[c]) cls_of[(size_t)s] = (int)c;
-  long long scratch = 0;
   for (int64_t s = 0; s < p.r_count; ++s) {
     RqSignal& g = sigs[(size_t)s];
     memset(&g, 0, sizeof(g));
     g.in_bytes = p.r_in_off[(size_t)s] * (long long)p.in_elem;
     g.out_bin = p.r_out_off[(size_t)s];
-    const RqClass& k = cls[(size_t)cls_of[(size_t)s]];
-    if ((int64_t)k.P * k.Np > kRqTilePoints) {
-      g.scratch = scratch;
-      scratch += (long long)k.P * k.Np;
-      const int rpt = std::min(k.P, kRqTilePoints / k.Np);
-      g.nfft = (k.P + rpt - 1) / rpt;
-      split.push_back({-k.M, s});
-    }
-  }
-  std::sort(split.begin(), split.end());
-  auto unpack_tiles = [&](int64_t s) {
-    const int c = cls_of[(size_t)s];
-    const RqClass& k = cls[(size_t)c];
-    const int jt = k.real_packed ? k.Mc / 2 + 1 : k.Mc;
-    for (int j0 = 0; j0 < jt; j0 += kRqLeadersPerTile)
-      tiles.push_back(RqTile{kRqUnpack, c, (int)s, j0, std::min(jt, j0 + kRqLeadersPerTile), 0});
-  };
-  // a signal's unpack tiles follow its last fft tile by at least `lag` fft tiles (about one
-  // wave of resident CTAs), so that an unpack tile seldom waits for fft tiles still running
-  std::vector<std::pair<size_t, int64_t>> pending;   // (tiles emitted after its fft tiles, signal)
-  size_t next = 0;
-  for (size_t i = 0; i < split.size(); ++i) {
-    const int64_t s = split[i].second;
-    const int c = cls_of[(size_t)s];
-    const RqClass& k = cls[(size_t)c];
-    const int rpt = std::min(k.P, kRqTilePoints / k.Np);
-    for (int r = 0; r < k.P; r += rpt) tiles.push_back(RqTile{kRqFft, c, (int)s, r, std::min(rpt, k.P - r), 0});
-    pending.push_back({tiles.size(), s});
-    while (next < pending.size() && pending[next].first + (size_t)lag <= tiles.size()) unpack_tiles(pending[next++].second);
-  }
-  while (next < pending.size()) unpack_tiles(pending[next++].second);
-  std::vector<std::pair<int64_t, size_t>> corder;
-  for (size_t c = 0; c < ncls; ++c) {
-    const RqClass& k = cls[c];
-    if ((int64_t)k.P * k.Np > kRqTilePoints) continue;
-    corder.push_back({-(int64_t)members[c].size() * (k.M + p.r_sub[c]->p.N), c});
-  }
-  std::sort(corder.begin(), corder.end());
-  for (auto& co : corder) {
-    const size_t c = co.second;
-    const RqClass& k = cls[c];
-    const int per = whole_group(k);
-    for (size_t i = 0; i < members[c].size(); i += per) {
-      const int cnt = (int)std::min<size_t>(per, members[c].size() - i);
-      tiles.push_back(RqTile{kRqWhole, (int)c, (int)whole.size(), 0, cnt, 0});
-      for (int w = 0; w < cnt; ++w) whole.push_back((int)members[c][i + w]);
-    }
+    g.scratch = lay.scratch[(size_t)s];
+    g.nfft = lay.nfft[(size_t)s];
   }
   if (tiles.size() > 0x7fffffff || p.r_count > 0x7ffffffe) return ADFFT_ERR_UNSUPPORTED_SIZE;
 
@@ -346,6 +381,68 @@ int launch_queue(Plan& p, const void* in, void* out, cudaStream_t s) {
 }
 
 }  // namespace
+
+// The queue layout of a ragged batch from its shapes alone (host only, no CUDA call): the shape
+// classes are formed and ordered as a ragged plan forms them ((N, M) in increasing order).
+int ragged_queue_layout(const int64_t* N, const double* alpha, int64_t count, int dtype, int lag,
+                        int32_t* tiles_out, int64_t tile_capacity, int64_t* ntiles, int64_t* whole_out,
+                        int64_t whole_capacity, int64_t* nwhole) {
+  if (!N || !alpha || count < 0 || lag < 0 || !ntiles || !nwhole) return ADFFT_ERR_INVALID_ARG;
+  if (dtype != ADFFT_R32 && dtype != ADFFT_C64) return ADFFT_ERR_NOT_SUPPORTED;
+  std::map<std::pair<int64_t, int64_t>, std::vector<int64_t>> classes;
+  for (int64_t i = 0; i < count; ++i) {
+    const double a = alpha[i];
+    if (N[i] < 1) return ADFFT_ERR_INVALID_ARG;
+    if (!(a > 0.0) || !isfinite(a)) return ADFFT_ERR_INVALID_ALPHA;
+    const double Md = a * (double)N[i];
+    const double Mr = nearbyint(Md);
+    if (fabs(Md - Mr) > 1e-9 * Md || Mr < 1.0) return ADFFT_ERR_INVALID_ALPHA;
+    classes[{N[i], (int64_t)Mr}].push_back(i);
+  }
+  std::vector<RqClass> cls;
+  std::vector<std::vector<int64_t>> members;
+  for (auto& kv : classes) {
+    const int64_t n = kv.first.first, m = kv.first.second;
+    int mode;
+    int64_t Nc, Mc;
+    if (dtype == ADFFT_C64) {
+      mode = kLoadComplex;
+      Nc = n;
+      Mc = m;
+    } else if (n % 2 == 0 && m % 2 == 0) {
+      mode = kLoadRealPacked;
+      Nc = n / 2;
+      Mc = m / 2;
+    } else {
+      return ADFFT_ERR_NOT_SUPPORTED;
+    }
+    RqClass k;
+    if (rq_geometry(mode, Nc, Mc, m, k) != ADFFT_OK) return ADFFT_ERR_NOT_SUPPORTED;
+    cls.push_back(k);
+    members.push_back(kv.second);
+  }
+  RqLayout lay;
+  rq_layout(cls, members, count, lag, lay);
+  *ntiles = (int64_t)lay.tiles.size();
+  *nwhole = (int64_t)lay.whole.size();
+  if (tiles_out) {
+    if (tile_capacity < *ntiles) return ADFFT_ERR_INVALID_ARG;
+    for (size_t i = 0; i < lay.tiles.size(); ++i) {
+      const RqTile& t = lay.tiles[i];
+      int32_t* o = tiles_out + 5 * i;
+      o[0] = t.kind;
+      o[1] = t.cls;
+      o[2] = t.sig;
+      o[3] = t.a0;
+      o[4] = t.a1;
+    }
+  }
+  if (whole_out) {
+    if (whole_capacity < *nwhole) return ADFFT_ERR_INVALID_ARG;
+    for (size_t i = 0; i < lay.whole.size(); ++i) whole_out[i] = lay.whole[i];
+  }
+  return ADFFT_OK;
+}
 
 int ragged_set_form(Plan& p, int form) {
   if (form == ADFFT_RAGGED_QUEUE && !p.rq_ok) return ADFFT_ERR_NOT_SUPPORTED;
